@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Throughput of the FS2D HLF hot path (arXiv 2103.00693) on GB300.
+
+Workload: the all-connected 6 x 6 grid (n = 36, Bernoulli(1/2) diagonal,
+seed 3, binary rank r = 36). One step is one pass over every part of the
+path through the C ABI:
+  hlf_factor (stage 1: GF(2) elimination, kernel basis, q, z^a)
+  hlf_enumerate_reduce of all 2^r solutions (count, XOR-fold, hash sum)
+  hlf_enumerate_store of the first 2^30 solutions into HBM (8 GiB)
+  hlf_sample of 2^20 seeded indices.
+value = 2^r solutions per step / step time (the store and the sample are
+extra work inside the step and are not counted as solutions).
+
+Other legs on the same JSON line: the dominant kernel's roofline, the store
+kernel's HBM roofline, an end-to-end run through host buffers (e2e), SM
+clocks sampled during the timed region, and the CPU oracle timed on the host
+cores (cpu_baseline). `--impl reference` times the CPU oracle alone.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FS2D HLF solutions/sec"
+UNIT = "solutions/s"
+# 32-bit integer instructions per solution of the reduce at W = 1: Gray step
+# XOR 2, fold XOR 2, SplitMix64 finalizer 18 (three 64-bit xor-shifts at 4,
+# two 64 x 64 -> 64 multiplies at 3), 64-bit add of the hash 2.
+OPS_PER_SOLUTION_W1 = 24
+ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
+STORE_LOG2 = 30
+SAMPLE_LOG2 = 20
+SAMPLE_SEED = 99
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["hlf", "reference"], default="hlf")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-oracle sample")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.split(",") for ln in self.file.read().strip().splitlines() if ln.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if (args.impl == "hlf" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_sample(target_s: float):
+    """Time the oracle as it stands (factor + reduce of a leading window of
+    the workload) on all host cores; the window is sized for ~target_s."""
+    from oracle import cpu as oc
+    from synth import workloads as wl
+
+    cores = os.cpu_count() or 1
+    A = wl.grid6()
+    F = oc.factor(A)
+    t0 = time.perf_counter()
+    oc.reduce(F, 0, 1 << 24, cores)
+    rate = (1 << 24) / max(time.perf_counter() - t0, 1e-6)
+    k = 24
+    while k < F.r and (1 << (k + 1)) / rate <= target_s:
+        k += 1
+    t0 = time.perf_counter()
+    F = oc.factor(A)
+    oc.reduce(F, 0, 1 << k, cores)
+    dt = time.perf_counter() - t0
+    return {"value": (1 << k) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle factor + reduce of solutions [0, 2^{k}) of the 2^{F.r} on {cores} threads "
+                      f"({dt:.1f} s)"}, k
+
+
+def workload_config(r: int):
+    return {"workload": "grid6x6 all-connected (n=36, Bernoulli(1/2) diagonal, seed 3)",
+            "n": 36, "r": r, "reduce_per_step": f"2^{r}", "store_per_step": f"2^{STORE_LOG2}",
+            "sample_per_step": f"2^{SAMPLE_LOG2}",
+            "l2": "each step stores 8 GiB (> 129 MB L2) between reduces; no separate flush",
+            "parallelism": "replicas (one independent instance per GPU)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    from oracle import cpu as oc
+    from synth import workloads as wl
+
+    A = wl.grid6()
+    F = oc.factor(A)
+    # one step = oracle factor + reduce of a leading 2^k window (~4 s)
+    t0 = time.perf_counter()
+    oc.reduce(F, 0, 1 << 24, cores)
+    rate = (1 << 24) / max(time.perf_counter() - t0, 1e-6)
+    k = 24
+    while k < F.r and (1 << (k + 1)) / rate <= 4.0:
+        k += 1
+
+    def step():
+        G = oc.factor(A)
+        oc.reduce(G, 0, 1 << k, cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = args.steps * (1 << k) / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": workload_config(F.r),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: oracle factor + reduce of solutions [0, 2^{k}) of the "
+                                       f"2^{F.r} on {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU path
+
+def run_hlf(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2103_00693_gb300 as hlf
+    import synth
+    from synth import workloads as wl
+
+    torch.cuda.set_device(local)
+    hlf.load()
+    dev = torch.device("cuda", local)
+    A = wl.grid6()
+    n = A.shape[0]
+    W = hlf.words(n)
+    packed = hlf.pack_rows(A).view(np.int64)
+    A_dev = torch.from_numpy(packed).to(dev)
+    h = hlf.hlf_factor(A_dev, n)
+    r = hlf.hlf_get_rank(h)
+    hlf.hlf_destroy(h)
+    total = 1 << min(r, 64)
+    store_n = min(1 << STORE_LOG2, total)
+    m = 1 << SAMPLE_LOG2
+    idx_host = synth.sample_indices(SAMPLE_SEED, m, 0, total).view(np.int64)
+    idx_dev = torch.from_numpy(idx_host).to(dev)
+    out = torch.empty((store_n, W), dtype=torch.int64, device=dev)
+    smp = torch.empty((m, W), dtype=torch.int64, device=dev)
+    red = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        hh = hlf.hlf_factor(A_dev, n, stream)
+        if evs:
+            evs[0].record(stream)
+        hlf.hlf_enumerate_reduce(hh, 0, total, red, stream)
+        if evs:
+            evs[1].record(stream)
+        hlf.hlf_enumerate_store(hh, 0, store_n, out, stream)
+        if evs:
+            evs[2].record(stream)
+        hlf.hlf_sample(hh, idx_dev, m, smp, stream)
+        hlf.hlf_destroy(hh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    res = hlf.ReduceResult.from_words(red.cpu().numpy(), W)
+    if res.count != total:
+        raise RuntimeError(f"reduce counted {res.count} solutions, expected {total}")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier(world)
+    ms = start.elapsed_time(end)
+    ms_max = max_over_ranks(ms, world)
+    reduce_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    store_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    value = world * args.steps * total / (ms_max / 1e3)
+
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * ISSUE_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 / 1e12  # Tops/s
+    ops = total * OPS_PER_SOLUTION_W1 * W
+    achieved = ops / (reduce_ms / 1e3) / 1e12
+    store_bytes = store_n * W * 8
+    store_gbs = store_bytes / (store_ms / 1e3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(r),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "kernel": "reduce_kernel<1,4>",
+                         "ms_per_launch": reduce_ms,
+                         "peak_basis": f"{sms} SMs x {ISSUE_LANES_PER_SM_CLK} int32 lanes/clk x "
+                                       f"{pk['sm_max_mhz']:.0f} MHz (issue limit)",
+                         "ops_per_solution": OPS_PER_SOLUTION_W1 * W},
+            "roofline_store": {"bound": "hbm", "achieved": store_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                               "frac": store_gbs / pk["hbm_gbs"], "traffic": None,
+                               "kernel": "store_kernel<1,2>", "ms_per_launch": store_ms,
+                               "peak_source": pk["source"]},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk}
+
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, world, dev, A, r, total, store_n, idx_host)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], _ = cpu_oracle_sample(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
+    """The same step through the C ABI from host buffers: A and the sample
+    indices are copied in from pinned memory, the 2^30 stored solutions, the
+    samples and the reduce result are copied back, all inside the timed
+    region."""
+    import numpy as np
+    import torch
+
+    import paper_2103_00693_gb300 as hlf
+
+    n = A.shape[0]
+    W = hlf.words(n)
+    A_host = torch.from_numpy(hlf.pack_rows(A).view(np.int64)).pin_memory()
+    idx_pin = torch.from_numpy(idx_host).pin_memory()
+    m = idx_pin.numel()
+    A_dev = torch.empty_like(A_host, device=dev)
+    idx_dev = torch.empty_like(idx_pin, device=dev)
+    out = torch.empty((store_n, W), dtype=torch.int64, device=dev)
+    smp = torch.empty((m, W), dtype=torch.int64, device=dev)
+    red = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, device=dev)
+    out_host = torch.empty((store_n, W), dtype=torch.int64, pin_memory=True)
+    smp_host = torch.empty((m, W), dtype=torch.int64, pin_memory=True)
+    red_host = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, pin_memory=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        A_dev.copy_(A_host, non_blocking=True)
+        idx_dev.copy_(idx_pin, non_blocking=True)
+        hh = hlf.hlf_factor(A_dev, n, stream)
+        hlf.hlf_enumerate_reduce(hh, 0, total, red, stream)
+        hlf.hlf_enumerate_store(hh, 0, store_n, out, stream)
+        out_host.copy_(out, non_blocking=True)
+        hlf.hlf_sample(hh, idx_dev, m, smp, stream)
+        smp_host.copy_(smp, non_blocking=True)
+        red_host.copy_(red, non_blocking=True)
+        hlf.hlf_destroy(hh)
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    barrier(world)
+    if int(red_host[0]) != total:
+        raise RuntimeError("e2e reduce count mismatch")
+    h2d = A_host.numel() * 8 + idx_pin.numel() * 8
+    d2h = out_host.numel() * 8 + smp_host.numel() * 8 + red_host.numel() * 8
+    return {"value": world * args.steps * total / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / args.steps}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_hlf(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * hlf.h -- C ABI of the GB300 (sm_103a) solver for the full-sampling 2D
+ * hidden linear function problem (FS2D HLF) of arXiv 2103.00693.
+ *
+ * Problem (Section 1): for a symmetric binary n x n matrix A, find every
+ * z in {0,1}^n with q(x) = 2 z^T x (mod 4) for all x in Ker(A), where
+ * q(x) = x^T A x (mod 4). The solutions form the affine space z^a + Col(A)
+ * of 2^r elements, r the binary rank (Section 2).
+ *
+ * The library runs the paper's two stages on one GPU:
+ *   stage 1 (the "CLA module" of Section 2, Fig. 1(b)) -- hlf_factor:
+ *     GF(2) elimination of A -> rank r, pivot columns P, a basis of Col(A),
+ *     q on a basis of Ker(A), and one particular solution z^a;
+ *   stage 2 (the "classical parallel circuit" of Section 2, Eqs. 1-3,
+ *     Fig. 1(c)) -- hlf_enumerate_*, hlf_sample: the solutions themselves.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Bit layout. A vector of n bits is W = ceil(n / 64) uint64 words; bit j
+ *   (0-based; the paper's z_{j+1}) is bit (j % 64) of word j / 64. Padding
+ *   bits (j >= n) are 0. A matrix is row-major [n][W]: bit j of row i is
+ *   A_{i+1, j+1}.
+ * Basis and order (a reading of Section 2, where the paper leaves both
+ *   open). B_0 .. B_{r-1} are the nonzero rows of the reduced row echelon
+ *   form of A, in increasing order of their pivot columns p_0 < ... < p_{r-1}
+ *   (P is the leftmost maximal independent column set L_ind of Section 2).
+ *   They span Row(A) = Col(A) = Ker(A)^perp. z^a (here z0) is the unique
+ *   solution that is 0 on every pivot column. Solution number i is
+ *       z(i) = z0 XOR  XOR_{k : bit k of g(i) is 1} B_k,   g(i) = i ^ (i >> 1),
+ *   the reflected Gray code, so z(i+1) = z(i) ^ B_{ctz(i+1)} and z(i)
+ *   restricted to P is g(i). Indices run over [0, 2^min(r, 64)): with
+ *   r > 64 only B_0 .. B_63 vary (documented limit, not an error).
+ * Memory. Every pointer named *_dev is device memory owned by the caller;
+ *   every *_host pointer is host memory owned by the caller. The library
+ *   owns an hlf_handle and the device buffers behind it until hlf_destroy.
+ * Streams. `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *   default stream). Work is enqueued asynchronously on it; calls that must
+ *   read results on the host say so.
+ * Errors. Every call returns an hlf_status and never throws or traps.
+ *   Arguments are checked on the host before anything is enqueued. Faults
+ *   found by a kernel (A not symmetric, padding bits set, an index outside
+ *   the space) are written to the handle's device status word and returned
+ *   by the next call that synchronises on the handle (hlf_get_rank,
+ *   hlf_get_factor, hlf_get_status, and the first enumerate call after
+ *   hlf_factor).
+ */
+#ifndef HLF_H
+#define HLF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hlf_status {
+    HLF_OK = 0,
+    HLF_ERR_ARG = 1,           /* null pointer, bad count, unknown option */
+    HLF_ERR_SIZE = 2,          /* n outside [1, HLF_MAX_N] */
+    HLF_ERR_NOT_SYMMETRIC = 3, /* A != A^T (the problem needs symmetric A, Section 1) */
+    HLF_ERR_PADDING = 4,       /* a padding bit (column >= n) is set */
+    HLF_ERR_RANGE = 5,         /* window or index outside [0, 2^min(r,64)) */
+    HLF_ERR_NOMEM = 6,         /* device or host allocation failed */
+    HLF_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
+    HLF_ERR_CUDA = 8,          /* a CUDA runtime call failed */
+    HLF_ERR_INTERNAL = 9       /* an invariant of the method failed (e.g. q odd on Ker(A)) */
+} hlf_status;
+
+#define HLF_MAX_N 1024      /* largest n (32 x 32 grids) */
+#define HLF_MAX_W 16        /* words per row at HLF_MAX_N */
+#define HLF_MAX_VARYING 64  /* basis vectors addressable by a 64-bit index */
+
+/* Result of a reduce over a window: the number of solutions, the sum mod 2^64
+ * of their hashes, and the XOR of all of them (words >= W are 0). The hash of
+ * a solution with words w_0..w_{W-1} is h = mix(w_0), then h = mix(h ^ w_j),
+ * with mix the SplitMix64 finalizer (Steele, Lea and Flood, OOPSLA 2014).
+ * All three are independent of the order in which solutions are visited. */
+typedef struct hlf_reduce {
+    uint64_t count;
+    uint64_t hsum;
+    uint64_t xor_fold[HLF_MAX_W];
+} hlf_reduce; /* 144 bytes */
+
+typedef struct hlf_handle hlf_handle;
+
+/* Text for a status code (static storage). */
+const char* hlf_status_string(hlf_status s);
+
+/* Number of CUDA devices visible, or -1 if the runtime cannot be reached. */
+int32_t hlf_device_count(void);
+
+/*
+ * Stage 1, the CLA module (Section 2, steps (1)-(4); Fig. 1(b)).
+ * A_dev:  [n][W] uint64, device, caller-owned; read until the factor kernel
+ *         ends (i.e. in stream order), not retained.
+ * n:      1 .. HLF_MAX_N.
+ * stream: cudaStream_t the kernel is launched on.
+ * *h:     receives a new handle (library-owned; free with hlf_destroy).
+ * Computes r, P, B_0..B_{r-1} and z0 on the device. Asynchronous: symmetry
+ * and padding faults surface on the first synchronising call on *h.
+ * Returns HLF_ERR_SIZE for bad n, HLF_ERR_ARG for null pointers,
+ * HLF_ERR_NOMEM / HLF_ERR_CUDA when allocation or launch fails (then *h is
+ * left NULL).
+ */
+hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle** h);
+
+/* Waits for the factorisation of h and returns its binary rank in *r, or the
+ * device-side fault (HLF_ERR_NOT_SYMMETRIC, HLF_ERR_PADDING, ...). */
+hlf_status hlf_get_rank(hlf_handle* h, int32_t* r);
+
+/* Waits for the factorisation and copies it to host memory (any pointer may
+ * be NULL to skip it): piv_host[r] int32 pivot columns (0-based, ascending),
+ * z0_host[W], basis_host[r][W] (B_k, row-major). */
+hlf_status hlf_get_factor(hlf_handle* h, int32_t* piv_host, uint64_t* z0_host, uint64_t* basis_host);
+
+/* n and W of the handle's matrix. */
+hlf_status hlf_get_shape(hlf_handle* h, int32_t* n, int32_t* W);
+
+/* Waits for all work enqueued so far through h and returns its device status
+ * word (HLF_OK if no kernel reported a fault), then clears it. */
+hlf_status hlf_get_status(hlf_handle* h);
+
+/*
+ * Stage 2, materialised (Section 2, Fig. 1(c): the solutions y ^ z^a one by
+ * one). Writes z(offset + t) to out_dev[t][0..W) for t in [0, count).
+ * out_dev: device, caller-owned, count * W uint64, 16-byte aligned.
+ * Requires offset + count <= 2^min(r, 64) (else HLF_ERR_RANGE, nothing
+ * enqueued). count = 0 is a no-op. The first call after hlf_factor waits
+ * for the factorisation (it needs r on the host).
+ */
+hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev,
+                               void* stream);
+
+/*
+ * Stage 2, reduced on the device: *red_dev (device, caller-owned, one
+ * hlf_reduce) is overwritten with (count, hash sum, XOR-fold) of the window
+ * [offset, offset + count). Same range rule as hlf_enumerate_store.
+ */
+hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, hlf_reduce* red_dev,
+                                void* stream);
+
+/*
+ * Stage 2, reduced per chunk: red_dev[c] (device, n_chunks entries) is
+ * overwritten with the reduce of [offset + c*chunk, offset + (c+1)*chunk).
+ * Requires chunk >= 1 and offset + n_chunks*chunk <= 2^min(r, 64) without
+ * overflow. The chunks combine (+, +, XOR) to the reduce of the whole range.
+ */
+hlf_status hlf_enumerate_reduce_chunks(hlf_handle* h, uint64_t offset, uint64_t chunk,
+                                       uint64_t n_chunks, hlf_reduce* red_dev, void* stream);
+
+/*
+ * Stage 2 at chosen indices: out_dev[t][0..W) = z(idx_dev[t]) for t < m.
+ * idx_dev: device uint64[m]; out_dev: device uint64[m][W]. An index outside
+ * the space yields an all-zero row and sets HLF_ERR_RANGE in the handle's
+ * status word (reported by hlf_get_status).
+ */
+hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64_t* out_dev,
+                      void* stream);
+
+/* Frees the handle and its device buffers (waits for its work first).
+ * NULL is accepted. */
+hlf_status hlf_destroy(hlf_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HLF_H */

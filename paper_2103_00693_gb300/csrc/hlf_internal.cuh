@@ -1,0 +1,64 @@
+// Internal declarations shared by the kernels and the C ABI of libhlf.
+//
+// Device-side layout of one factorisation (all written by the factor kernel):
+//   info  [16] int32   info[0] = status (hlf_status), info[1] = rank r
+//   piv   [n]  int32   pivot columns p_0 < ... < p_{r-1}
+//   basis [n][W]       B_0 .. B_{r-1}: the nonzero RREF rows in pivot order
+//   table [66][W]      enumeration table: rows 0..64 hold B_0 .. B_63 with the
+//                      rows k >= min(r, 64) zero (row 64 is always zero, it is
+//                      the target of ctz = 64 steps), row 65 holds z0.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hlf.h"
+
+namespace hlf {
+
+constexpr int kTableRows = 65;      // B_0..B_64 (row 64 always zero)
+constexpr int kTableZ0Row = 65;     // z0 follows the basis rows
+constexpr int kTableTotalRows = 66;
+
+struct FactorOut {
+    uint64_t* basis;  // [n][W]
+    int32_t* piv;     // [n]
+    uint64_t* table;  // [66][W]
+    int32_t* info;    // [16]
+};
+
+// ---------------------------------------------------------------- launchers
+hlf_status launch_factor(const uint64_t* A, int n, int W, const FactorOut& o, cudaStream_t s);
+hlf_status launch_reduce(const uint64_t* table, int W, uint64_t offset, uint64_t count,
+                         hlf_reduce* out, cudaStream_t s);
+hlf_status launch_reduce_chunks(const uint64_t* table, int W, uint64_t offset, uint64_t chunk,
+                                uint64_t n_chunks, hlf_reduce* out, cudaStream_t s);
+hlf_status launch_store(const uint64_t* table, int W, uint64_t offset, uint64_t count,
+                        uint64_t* out, cudaStream_t s);
+hlf_status launch_sample(const uint64_t* table, int W, int nb, const uint64_t* idx, uint64_t m,
+                         uint64_t* out, int32_t* info, cudaStream_t s);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// ----------------------------------------------------------- device helpers
+
+// SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014): the
+// finalizer the reduce applies to every solution word.
+__device__ __forceinline__ uint64_t mix64(uint64_t x)
+{
+    x ^= x >> 30;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27;
+    x *= 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return x;
+}
+
+// Index of the lowest set bit; 64 for x == 0 (so the zero row 64 is used).
+__device__ __forceinline__ int ctz64(uint64_t x) { return __clzll(__brevll(x)); }
+
+// Record the first device-side fault in a status word.
+__device__ __forceinline__ void set_status(int32_t* info, int code) { atomicCAS(info, 0, code); }
+
+}  // namespace hlf

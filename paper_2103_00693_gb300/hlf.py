@@ -1,0 +1,286 @@
+"""Python binding of libhlf's C ABI (include/hlf.h), with the same names.
+
+Argument marshalling only: tensors become device pointers, streams become
+cudaStream_t handles, status codes become exceptions. Every step of the
+solver runs in the library's CUDA kernels; there is no CPU fallback, and
+loading fails loudly if libhlf.so has not been built.
+
+Bit layout (as in hlf.h): an n-bit vector is W = ceil(n/64) uint64 words,
+bit j in word j // 64 at position j % 64. Device buffers are torch.int64
+tensors used as raw 64-bit storage.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MAX_N = 1024
+MAX_W = 16
+REDUCE_WORDS = 2 + MAX_W  # hlf_reduce: count, hsum, xor_fold[16]
+
+STATUS = {
+    0: "HLF_OK", 1: "HLF_ERR_ARG", 2: "HLF_ERR_SIZE", 3: "HLF_ERR_NOT_SYMMETRIC",
+    4: "HLF_ERR_PADDING", 5: "HLF_ERR_RANGE", 6: "HLF_ERR_NOMEM", 7: "HLF_ERR_TIMEOUT",
+    8: "HLF_ERR_CUDA", 9: "HLF_ERR_INTERNAL",
+}
+
+# Every entry point of include/hlf.h, with its ctypes signature.
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_i32 = ctypes.c_int32
+SIGNATURES = {
+    "hlf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hlf_device_count": (_i32, []),
+    "hlf_factor": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_vp)]),
+    "hlf_get_rank": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    "hlf_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "hlf_get_shape": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "hlf_get_status": (ctypes.c_int, [_vp]),
+    "hlf_enumerate_store": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
+    "hlf_enumerate_reduce": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
+    "hlf_enumerate_reduce_chunks": (ctypes.c_int, [_vp, _u64, _u64, _u64, _vp, _vp]),
+    "hlf_sample": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp]),
+    "hlf_destroy": (ctypes.c_int, [_vp]),
+}
+
+
+class HlfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libhlf.so. Raises if it is missing (unless build_if_missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"libhlf.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise HlfError(st, where)
+
+
+def _stream_ptr(stream) -> int | None:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream or None
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def words(n: int) -> int:
+    return (n + 63) // 64
+
+
+def pack_rows(A: np.ndarray) -> np.ndarray:
+    """Pack a dense 0/1 matrix [rows, n] into uint64 words [rows, W] (host-side
+    argument marshalling for hlf_factor)."""
+    A = np.asarray(A, dtype=np.uint8)
+    rows, n = A.shape
+    W = words(n)
+    padded = np.zeros((rows, W * 64), dtype=np.uint8)
+    padded[:, :n] = A
+    bits = np.packbits(padded.reshape(rows, W, 64), axis=2, bitorder="little")  # [rows, W, 8]
+    return bits.view("<u8").reshape(rows, W).astype(np.uint64)
+
+
+def unpack_rows(words_: np.ndarray, n: int) -> np.ndarray:
+    w = np.ascontiguousarray(np.asarray(words_, dtype=np.uint64))
+    if w.ndim == 1:
+        w = w[:, None]
+    b = np.unpackbits(w.view(np.uint8).reshape(w.shape[0], -1), axis=1, bitorder="little")
+    return b[:, :n]
+
+
+@dataclass
+class ReduceResult:
+    count: int
+    hsum: int
+    xor_fold: np.ndarray  # uint64 [W]
+
+    @staticmethod
+    def from_words(r, W: int) -> "ReduceResult":
+        r = np.asarray(r).astype(np.int64).view(np.uint64)
+        return ReduceResult(int(r[0]), int(r[1]), r[2:2 + W].copy())
+
+
+# ----------------------------------------------------------------- entry points
+
+def hlf_status_string(status: int) -> str:
+    return load().hlf_status_string(status).decode()
+
+
+def hlf_device_count() -> int:
+    return int(load().hlf_device_count())
+
+
+def hlf_factor(A_dev, n: int, stream=None) -> int:
+    """Stage 1 (CLA module): A_dev is a CUDA int64 tensor [n, W]; returns the
+    handle (an opaque pointer value)."""
+    if not A_dev.is_cuda or A_dev.dtype.itemsize != 8 or not A_dev.is_contiguous():
+        raise ValueError("A_dev must be a contiguous 64-bit CUDA tensor [n, W]")
+    h = _vp()
+    _check(load().hlf_factor(_ptr(A_dev), n, _stream_ptr(stream), ctypes.byref(h)), "hlf_factor")
+    return h.value
+
+
+def hlf_get_rank(h: int) -> int:
+    r = _i32()
+    _check(load().hlf_get_rank(h, ctypes.byref(r)), "hlf_get_rank")
+    return r.value
+
+
+def hlf_get_shape(h: int) -> tuple[int, int]:
+    n, W = _i32(), _i32()
+    _check(load().hlf_get_shape(h, ctypes.byref(n), ctypes.byref(W)), "hlf_get_shape")
+    return n.value, W.value
+
+
+def hlf_get_factor(h: int):
+    """(piv int32[r], z0 uint64[W], basis uint64[r, W]) copied to the host."""
+    r = hlf_get_rank(h)
+    _, W = hlf_get_shape(h)
+    piv = np.zeros(max(r, 1), dtype=np.int32)
+    z0 = np.zeros(W, dtype=np.uint64)
+    basis = np.zeros((max(r, 1), W), dtype=np.uint64)
+    _check(load().hlf_get_factor(h, piv.ctypes.data, z0.ctypes.data, basis.ctypes.data), "hlf_get_factor")
+    return piv[:r], z0, basis[:r]
+
+
+def hlf_get_status(h: int) -> int:
+    return int(load().hlf_get_status(h))
+
+
+def hlf_enumerate_store(h: int, offset: int, count: int, out_dev, stream=None):
+    _check(load().hlf_enumerate_store(h, offset, count, _ptr(out_dev) if out_dev is not None else None,
+                                      _stream_ptr(stream)), "hlf_enumerate_store")
+
+
+def hlf_enumerate_reduce(h: int, offset: int, count: int, red_dev, stream=None):
+    _check(load().hlf_enumerate_reduce(h, offset, count, _ptr(red_dev), _stream_ptr(stream)),
+           "hlf_enumerate_reduce")
+
+
+def hlf_enumerate_reduce_chunks(h: int, offset: int, chunk: int, n_chunks: int, red_dev, stream=None):
+    _check(load().hlf_enumerate_reduce_chunks(h, offset, chunk, n_chunks,
+                                              _ptr(red_dev) if red_dev is not None else None,
+                                              _stream_ptr(stream)), "hlf_enumerate_reduce_chunks")
+
+
+def hlf_sample(h: int, idx_dev, m: int, out_dev, stream=None):
+    _check(load().hlf_sample(h, _ptr(idx_dev) if idx_dev is not None else None, m,
+                             _ptr(out_dev) if out_dev is not None else None, _stream_ptr(stream)),
+           "hlf_sample")
+
+
+def hlf_destroy(h: int):
+    _check(load().hlf_destroy(h), "hlf_destroy")
+
+
+# ------------------------------------------------------------ convenience layer
+
+class Factorization:
+    """Owns one hlf_handle: the stage-1 result of one matrix, resident on the
+    device, from which any window of solutions can be enumerated."""
+
+    def __init__(self, A_dev, n: int, stream=None):
+        self.n = n
+        self.W = words(n)
+        self.h = hlf_factor(A_dev, n, stream)
+
+    @classmethod
+    def from_dense(cls, A: np.ndarray, device="cuda", stream=None) -> "Factorization":
+        import torch
+
+        packed = pack_rows(A)
+        A_dev = torch.from_numpy(packed.view(np.int64)).to(device)
+        f = cls(A_dev, A.shape[0], stream)
+        f._keep = A_dev  # A must stay alive until the factor kernel has run
+        return f
+
+    @property
+    def rank(self) -> int:
+        return hlf_get_rank(self.h)
+
+    def space_log2(self) -> int:
+        return min(self.rank, 64)
+
+    def factor_host(self):
+        return hlf_get_factor(self.h)
+
+    def store(self, offset: int, count: int, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty((count, self.W), dtype=torch.int64, device="cuda")
+        hlf_enumerate_store(self.h, offset, count, out, stream)
+        return out
+
+    def reduce(self, offset: int, count: int, red=None, stream=None):
+        import torch
+
+        if red is None:
+            red = torch.empty(REDUCE_WORDS, dtype=torch.int64, device="cuda")
+        hlf_enumerate_reduce(self.h, offset, count, red, stream)
+        return red
+
+    def reduce_chunks(self, offset: int, chunk: int, n_chunks: int, red=None, stream=None):
+        import torch
+
+        if red is None:
+            red = torch.empty((n_chunks, REDUCE_WORDS), dtype=torch.int64, device="cuda")
+        hlf_enumerate_reduce_chunks(self.h, offset, chunk, n_chunks, red, stream)
+        return red
+
+    def sample(self, idx_dev, out=None, stream=None):
+        import torch
+
+        m = idx_dev.numel()
+        if out is None:
+            out = torch.empty((m, self.W), dtype=torch.int64, device="cuda")
+        hlf_sample(self.h, idx_dev, m, out, stream)
+        return out
+
+    def status(self) -> int:
+        return hlf_get_status(self.h)
+
+    def close(self):
+        if self.h:
+            hlf_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,94 @@
+"""Stage 1 on the GPU (hlf_factor) against the oracle, bit-exact: rank,
+pivot columns, RREF basis rows and z^a, plus the device-side input checks."""
+
+import numpy as np
+import pytest
+
+import paper_2103_00693_gb300 as hlf
+import synth
+from oracle import cpu as oc
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    c = []
+    for N in (2, 3, 4, 5, 6, 8, 11, 16, 23, 32):
+        c.append((f"grid{N}-p.5", synth.grid_instance(N, 0.5, 10 + N)))
+        c.append((f"grid{N}-full", synth.grid_instance(N, 1.0, 20 + N)))
+    for N in (2, 3, 4, 5):
+        for b in synth.paper_b_patterns(N * N):
+            c.append((f"paper{N}-{b[-2:]}", synth.all_connected(N, b)))
+    # W boundaries and general symmetric matrices (§5: any symmetric A)
+    for n in (1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 511, 512, 513, 777, 1023, 1024):
+        c.append((f"sym{n}", synth.random_symmetric(n, 0.3, n)))
+    for n in (1, 64, 100, 1024):
+        c.append((f"zero{n}", np.zeros((n, n), dtype=np.uint8)))
+        c.append((f"eye{n}", np.eye(n, dtype=np.uint8)))
+    c.append(("sparse300", synth.random_symmetric(300, 0.01, 3)))
+    c.append(("dense1000", synth.random_symmetric(1000, 0.9, 4)))
+    return c
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name,A", CASES, ids=[c[0] for c in CASES])
+def test_factor_parity(cuda_ok, name, A):
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    try:
+        assert G.rank == F.r
+        piv, z0, basis = G.factor_host()
+        assert np.array_equal(piv, F.piv)
+        assert np.array_equal(z0, F.z0_words())
+        assert np.array_equal(basis, F.basis_words())
+        assert G.status() == 0
+    finally:
+        G.close()
+
+
+def test_factor_rejects_non_symmetric(cuda_ok):
+    A = synth.grid_instance(5, 0.5, 1)
+    A[3, 17] ^= 1
+    G = hlf.Factorization.from_dense(A)
+    with pytest.raises(hlf.HlfError) as e:
+        G.rank
+    assert e.value.status == 3
+    G.close()
+
+
+def test_factor_rejects_padding_bits(cuda_ok):
+    import torch
+
+    A = synth.grid_instance(5, 0.5, 2)  # n = 25, one word per row
+    packed = hlf.pack_rows(A)
+    packed[7, 0] |= np.uint64(1) << np.uint64(40)
+    A_dev = torch.from_numpy(packed.view(np.int64)).cuda()
+    h = hlf.hlf_factor(A_dev, 25)
+    with pytest.raises(hlf.HlfError) as e:
+        hlf.hlf_get_rank(h)
+    assert e.value.status == 4
+    hlf.hlf_destroy(h)
+
+
+def test_factor_size_limits(cuda_ok):
+    import torch
+
+    A_dev = torch.zeros((1025, 17), dtype=torch.int64, device="cuda")
+    with pytest.raises(hlf.HlfError) as e:
+        hlf.hlf_factor(A_dev, 1025)
+    assert e.value.status == 2
+    with pytest.raises(hlf.HlfError):
+        hlf.hlf_factor(A_dev, 0)
+
+
+def test_many_handles_independent(cuda_ok):
+    """Several factorisations in flight on one stream stay independent."""
+    mats = [synth.grid_instance(N, 0.5, 900 + N) for N in (3, 7, 12, 20, 31)]
+    Gs = [hlf.Factorization.from_dense(A) for A in mats]
+    for A, G in zip(mats, Gs):
+        F = oc.factor(A)
+        piv, z0, basis = G.factor_host()
+        assert G.rank == F.r and np.array_equal(basis, F.basis_words()) and np.array_equal(z0, F.z0_words())
+        G.close()

@@ -33,10 +33,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FS2D HLF solutions/sec"
 UNIT = "solutions/s"
-# 32-bit integer instructions per solution of the reduce at W = 1: Gray step
-# XOR 2, fold XOR 2, SplitMix64 finalizer 18 (three 64-bit xor-shifts at 4,
-# two 64 x 64 -> 64 multiplies at 3), 64-bit add of the hash 2.
-OPS_PER_SOLUTION_W1 = 24
+# Minimal 32-bit integer instructions per solution of the reduce at W = 1:
+# Gray step XOR 2, fold XOR 2, the SplitMix64 finalizer after its first
+# (GF(2)-linear) layer, which the walk absorbs into the basis table: two
+# 64 x 64 -> 64 multiplies at 3 and two 64-bit xor-shifts at 4 (14), and the
+# 64-bit add of the hash 2.
+OPS_PER_SOLUTION_W1 = 20
 ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
 STORE_LOG2 = 30
 SAMPLE_LOG2 = 20
@@ -46,12 +48,17 @@ SAMPLE_SEED = 99
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["hlf", "reference"], default="hlf")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-oracle sample")
+    p.add_argument("--reduce-log2", type=int, default=None,
+                   help="reduce only the first 2^k solutions (small cases for profiling; the line says so)")
+    p.add_argument("--store-log2", type=int, default=STORE_LOG2, help="solutions stored per step (log2)")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched (4096 grids) leg")
+    p.add_argument("--no-served", action="store_true", help="skip the served (Poisson stream) leg")
     return p.parse_args()
 
 
@@ -176,9 +183,12 @@ def cpu_oracle_sample(target_s: float):
                       f"({dt:.1f} s)"}, k
 
 
-def workload_config(r: int):
+def workload_config(r: int, reduce_n: int | None = None, store_n: int | None = None):
+    reduce_n = reduce_n or (1 << r)
+    store_n = store_n or (1 << STORE_LOG2)
     return {"workload": "grid6x6 all-connected (n=36, Bernoulli(1/2) diagonal, seed 3)",
-            "n": 36, "r": r, "reduce_per_step": f"2^{r}", "store_per_step": f"2^{STORE_LOG2}",
+            "n": 36, "r": r, "reduce_per_step": f"2^{reduce_n.bit_length() - 1}",
+            "store_per_step": f"2^{store_n.bit_length() - 1}",
             "sample_per_step": f"2^{SAMPLE_LOG2}",
             "l2": "each step stores 8 GiB (> 129 MB L2) between reduces; no separate flush",
             "parallelism": "replicas (one independent instance per GPU)"}
@@ -245,7 +255,9 @@ def run_hlf(args, world, rank, local):
     r = hlf.hlf_get_rank(h)
     hlf.hlf_destroy(h)
     total = 1 << min(r, 64)
-    store_n = min(1 << STORE_LOG2, total)
+    if args.reduce_log2 is not None:
+        total = min(total, 1 << args.reduce_log2)
+    store_n = min(1 << args.store_log2, total)
     m = 1 << SAMPLE_LOG2
     idx_host = synth.sample_indices(SAMPLE_SEED, m, 0, total).view(np.int64)
     idx_dev = torch.from_numpy(idx_host).to(dev)
@@ -304,7 +316,7 @@ def run_hlf(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(r),
+            "config": workload_config(r, total, store_n),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved / alu_peak, "traffic": None,
                          "kernel": "reduce_kernel<1,4>",
@@ -321,6 +333,12 @@ def run_hlf(args, world, rank, local):
 
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, world, dev, A, r, total, store_n, idx_host)
+    del out, smp
+    torch.cuda.empty_cache()
+    if not args.no_batched:
+        line["batched"] = run_batched(args)
+    if not args.no_served:
+        line["served"] = run_served(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], _ = cpu_oracle_sample(args.cpu_seconds)
     if rank == 0:
@@ -381,6 +399,72 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
     d2h = out_host.numel() * 8 + smp_host.numel() * 8 + red_host.numel() * 8
     return {"value": world * args.steps * total / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / args.steps}
+
+
+def run_batched(args):
+    """The batched workload: 4096 grids (N in 4..16, p = 1/2), each reducing
+    min(2^r, 2^20) solutions. One persistent launch per step, replayed from a
+    CUDA graph with autotuned tiles, against the plain path (factor + reduce
+    launches per grid)."""
+    import torch
+
+    from paper_2103_00693_gb300 import autotune
+    from paper_2103_00693_gb300.batch import Batch, per_instance
+    from synth import workloads as wl
+
+    mats = wl.batch()
+    cap = 1 << wl.BATCH_CAP_LOG2
+    B = Batch(mats)
+    tune = autotune.autotune(B, cap, reps=2)
+    B.capture(cap)
+    for _ in range(max(1, args.warmup)):
+        B.replay()
+    torch.cuda.synchronize()
+    reps = max(3, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        B.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    r, red = B.results()
+    sols = sum(x.count for x in red)
+    B.close()
+    per_instance(mats[:64], cap)  # warm the plain path
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ranks, _ = per_instance(mats, cap)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    return {"workload": "4096 grids, N uniform 4..16, p=1/2, min(2^r, 2^20) solutions each",
+            "ms_per_batch": ms, "inst_per_s": len(mats) / (ms / 1e3), "solutions_per_s": sols / (ms / 1e3),
+            "solutions_per_batch": sols, "tiles": {"ctas_per_sm": tune["tiles"][0], "chunk": tune["tiles"][1]},
+            "launch": "one persistent kernel (+3 memsets) replayed from a CUDA graph",
+            "plain_ms_per_batch": 1e3 * plain_s, "plain_inst_per_s": len(mats) / plain_s,
+            "speedup_vs_plain": plain_s / (ms / 1e3)}
+
+
+def run_served(args):
+    """The served workload: Poisson arrivals, N uniform 3..32, windows
+    log-uniform 2^10..2^24 solutions returned to pinned host memory. The
+    continuous-batching server and the plain one-request-at-a-time path see
+    the same streams at a low and a high arrival rate."""
+    from paper_2103_00693_gb300 import serve
+    from synth import workloads as wl
+
+    out = {"workload": "Poisson stream, N uniform 3..32 (n <= 1024), p=1/2, windows 2^10..2^24 to host"}
+    warm = wl.stream(8, 1000.0, seed=1)
+    srv = serve.Server(keep_results=False)
+    srv.run(warm)
+    serve.run_plain(warm, keep_results=False)
+    for name, rate, count in (("low_load", 50.0, 60), ("high_load", 2000.0, 200)):
+        reqs = wl.stream(count, rate)
+        st, _ = srv.run(reqs)
+        pl, _ = serve.run_plain(reqs, keep_results=False)
+        out[name] = {"rate_per_s": rate, "requests": count, "batched": st.summary(), "plain": pl.summary()}
+    srv.close()
+    return out
 
 
 def main():

@@ -161,6 +161,92 @@ hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64
  * NULL is accepted. */
 hlf_status hlf_destroy(hlf_handle* h);
 
+/* ------------------------------------------------------------ many windows
+ * Continuous batching for a request loop: windows of several factorisations
+ * (any n and W) materialised in ONE launch. Each window is exactly what
+ * hlf_enumerate_store writes; only the scheduling is shared.
+ */
+typedef struct hlf_many hlf_many;
+
+/* Plan for up to max_windows windows per call: two descriptor buffers on the
+ * device and two in pinned host memory (about 100 B per window each). */
+hlf_status hlf_many_create(int32_t max_windows, hlf_many** m);
+
+/*
+ * For j < k: writes z(offsets[j] + t) of handle hs[j] to outs_dev[j][t][0..W_j)
+ * for t < counts[j]. hs, offsets, counts and outs_dev are host arrays; each
+ * outs_dev[j] is device memory, 16-byte aligned, counts[j] * W_j words.
+ * Every window must lie inside its handle's index space (else HLF_ERR_RANGE,
+ * nothing enqueued). Waits for the handles' factorisations (their ranks are
+ * needed on the host) and for the call before last on this plan (its host
+ * staging buffer is reused); otherwise asynchronous on `stream`.
+ */
+hlf_status hlf_enumerate_store_many(hlf_many* m, hlf_handle* const* hs, const uint64_t* offsets,
+                                    const uint64_t* counts, uint64_t* const* outs_dev, int32_t k, void* stream);
+
+/* Frees the plan (waits for its launches). NULL is accepted. */
+hlf_status hlf_many_destroy(hlf_many* m);
+
+/* ------------------------------------------------------------------ batched
+ * Many independent matrices (the batched workload: thousands of grids of
+ * uneven n) factored (stage 1) and reduced (stage 2) in ONE persistent
+ * kernel launch. CTAs pull work items from an on-device queue: first one
+ * factorisation per matrix, then fixed-size chunks of each matrix's index
+ * space; a chunk waits, with a bounded number of polls, for its matrix's
+ * factorisation. The paper has no batched mode: this is the same arithmetic
+ * as hlf_factor + hlf_enumerate_reduce, scheduled across matrices.
+ */
+
+#define HLF_BATCH_MAX_N 256 /* largest n in a batch (one CTA of 256 threads per factorisation) */
+
+typedef struct hlf_batch hlf_batch;
+
+/* Creates a batch plan with device workspace for up to max_instances
+ * matrices (per matrix: a 66 x 4-word table, status, rank, a ready flag;
+ * about 2.1 KiB). The plan is bound to the current device. */
+hlf_status hlf_batch_create(int32_t max_instances, hlf_batch** b);
+
+/* Launch shape chosen by an autotuner: CTAs per SM (0 = as many as fit) and
+ * solutions per work item (a power of two >= 256). */
+hlf_status hlf_batch_set_tiles(hlf_batch* b, int32_t ctas_per_sm, uint64_t chunk);
+
+/* Bound on the polls a chunk makes while waiting for its matrix (default
+ * 2^23 polls of >= 128 ns); past it the chunk is skipped and the batch status
+ * becomes HLF_ERR_TIMEOUT. */
+hlf_status hlf_batch_set_spin_limit(hlf_batch* b, uint32_t polls);
+
+/* Fault injection for tests of the bounded waits: flags = 1 makes the next
+ * launches skip every factorisation item, so no chunk's matrix ever becomes
+ * ready and every wait runs out (HLF_ERR_TIMEOUT, results left unwritten).
+ * flags = 0 restores normal operation. No GPU fault is involved. */
+hlf_status hlf_batch_set_debug(hlf_batch* b, uint32_t flags);
+
+/*
+ * Factor and reduce `count` matrices in one launch (plus three memsets), all
+ * enqueued on `stream` with no host synchronisation (so it can be captured in
+ * a CUDA graph).
+ *   A_dev        device, the matrices' rows back to back: matrix b is
+ *                [n_b][W_b] words starting at word word_off_dev[b].
+ *   word_off_dev device int64[count]; n_dev device int32[count], each n_b in
+ *                [1, HLF_BATCH_MAX_N] (others fail alone with HLF_ERR_SIZE).
+ *   cap          each matrix reduces its solutions [0, min(2^min(r,64), cap)).
+ *   r_dev        device int32[count]: the rank, or -(hlf_status) if that
+ *                matrix failed (not symmetric, padding, size).
+ *   red_dev      device hlf_reduce[count], overwritten.
+ * Host-side errors: HLF_ERR_ARG (bad pointers, count > max_instances, plan
+ * made on another device), HLF_ERR_RANGE (too many work items).
+ */
+hlf_status hlf_batch_factor_reduce(hlf_batch* b, const uint64_t* A_dev, const int64_t* word_off_dev,
+                                   const int32_t* n_dev, int32_t count, uint64_t cap, int32_t* r_dev,
+                                   hlf_reduce* red_dev, void* stream);
+
+/* Waits for the plan's last launch and returns its status word (HLF_OK, or
+ * HLF_ERR_TIMEOUT if a bounded wait gave up), then clears it. */
+hlf_status hlf_batch_get_status(hlf_batch* b);
+
+/* Frees the plan (waits for its last launch). NULL is accepted. */
+hlf_status hlf_batch_destroy(hlf_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,107 @@
+"""Batched factorisation + reduction of many matrices in one persistent
+launch (hlf_batch_* in include/hlf.h), with CUDA-graph capture and the plain
+one-launch-per-matrix path it is compared with.
+
+Packing the matrices into one device buffer (rows back to back, a word
+offset and n per matrix) is argument marshalling; all solver work runs in
+the library's batch kernel.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import hlf
+
+
+class Batch:
+    """Device-resident batch of matrices and its plan (workspace)."""
+
+    def __init__(self, mats: list[np.ndarray], device: str = "cuda"):
+        import torch
+
+        self.count = len(mats)
+        self.ns = np.array([A.shape[0] for A in mats], dtype=np.int32)
+        if np.any(self.ns > hlf.BATCH_MAX_N) or np.any(self.ns < 1):
+            raise ValueError(f"batched matrices need 1 <= n <= {hlf.BATCH_MAX_N}")
+        self.Ws = (self.ns + 63) // 64
+        sizes = self.ns.astype(np.int64) * self.Ws
+        self.word_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        packed = np.concatenate([hlf.pack_rows(A).ravel() for A in mats]) if mats else np.zeros(0, np.uint64)
+        self.A_dev = torch.from_numpy(packed.view(np.int64)).to(device)
+        self.off_dev = torch.from_numpy(self.word_off).to(device)
+        self.n_dev = torch.from_numpy(self.ns).to(device)
+        self.r_dev = torch.empty(self.count, dtype=torch.int32, device=device)
+        self.red_dev = torch.empty((self.count, hlf.REDUCE_WORDS), dtype=torch.int64, device=device)
+        self.plan = hlf.hlf_batch_create(max(self.count, 1))
+        self.tiles = (0, 1 << 16)
+        self.graph = None
+
+    def set_tiles(self, ctas_per_sm: int, chunk: int):
+        hlf.hlf_batch_set_tiles(self.plan, ctas_per_sm, chunk)
+        self.tiles = (ctas_per_sm, chunk)
+
+    def run(self, cap: int, stream=None):
+        """Enqueue one launch: factor every matrix, reduce solutions
+        [0, min(2^r, cap)) of each."""
+        hlf.hlf_batch_factor_reduce(self.plan, self.A_dev, self.off_dev, self.n_dev, self.count, cap,
+                                    self.r_dev, self.red_dev, stream)
+
+    def capture(self, cap: int):
+        """Capture run(cap) into a CUDA graph; replay() re-runs it."""
+        import torch
+
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(cap, s)  # warm-up outside the graph
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.run(cap, s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def status(self) -> int:
+        return hlf.hlf_batch_get_status(self.plan)
+
+    def results(self):
+        """(ranks int32[count], list of ReduceResult)."""
+        r = self.r_dev.cpu().numpy()
+        red = self.red_dev.cpu().numpy()
+        return r, [hlf.ReduceResult.from_words(red[b], int(self.Ws[b])) for b in range(self.count)]
+
+    def close(self):
+        if self.plan:
+            hlf.hlf_batch_destroy(self.plan)
+            self.plan = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def per_instance(mats: list[np.ndarray], cap: int, device: str = "cuda"):
+    """The plain path: for each matrix, hlf_factor then hlf_enumerate_reduce of
+    [0, min(2^r, cap)) (one factor launch and one reduce launch per matrix; the
+    reduce needs r on the host, so each matrix waits for its factorisation).
+    Returns (ranks, reduce tensor [count, 18])."""
+    import torch
+
+    count = len(mats)
+    red = torch.empty((count, hlf.REDUCE_WORDS), dtype=torch.int64, device=device)
+    ranks = np.zeros(count, dtype=np.int32)
+    packed = [torch.from_numpy(hlf.pack_rows(A).view(np.int64)).to(device) for A in mats]
+    for b, A in enumerate(mats):
+        h = hlf.hlf_factor(packed[b], A.shape[0])
+        r = hlf.hlf_get_rank(h)
+        ranks[b] = r
+        total = min(1 << min(r, 64), cap)
+        hlf.hlf_enumerate_reduce(h, 0, total, red[b])
+        hlf.hlf_destroy(h)
+    return ranks, red

@@ -1,0 +1,220 @@
+// Device helpers of stage 2 (the classical parallel circuit of Section 2,
+// Eqs. 1-3, Fig. 1(c)), shared by the single-instance kernels and the batched
+// persistent kernel: the shared-memory enumeration table, seeding a run from
+// the definition z(i) = z0 ^ XOR_{k in g(i)} B_k, the reflected-Gray walk of a
+// run, the per-thread reduce accumulator and the block reduction.
+#pragma once
+
+#include "hlf_internal.cuh"
+
+namespace hlf {
+
+constexpr int kThreads = 256;
+
+template <int W>
+struct Table {
+    uint64_t B[kTableRows][W];  // B_0..B_63, zero rows beyond min(r,64), row 64 zero
+    uint64_t z0[W];
+};
+
+template <int W>
+__device__ __forceinline__ void load_table(Table<W>& t, const uint64_t* __restrict__ g)
+{
+    uint64_t* d = &t.B[0][0];
+    for (int i = threadIdx.x; i < kTableTotalRows * W; i += blockDim.x) d[i] = g[i];
+}
+
+// The first layer of the SplitMix64 finalizer, L(x) = x ^ (x >> 30), is
+// linear over GF(2), so it commutes with the walk's XORs:
+// L(z(i+1)) = L(z(i)) ^ L(B_ctz(i+1)). The reduce therefore walks y = L(z) on
+// word 0, with a table whose word-0 entries are L(B_k) and L(z0), and hashes
+// y with the remaining layers (mix_tail). Hash values are bit-identical to
+// mix64(z); the XOR-fold of word 0 is taken in the L domain and mapped back
+// once with L^-1(y) = y ^ (y >> 30) ^ (y >> 60).
+__device__ __forceinline__ uint64_t mix_head(uint64_t x) { return x ^ (x >> 30); }
+__device__ __forceinline__ uint64_t mix_head_inv(uint64_t y) { return y ^ (y >> 30) ^ (y >> 60); }
+__device__ __forceinline__ uint64_t mix_tail(uint64_t y)
+{
+    y *= 0xBF58476D1CE4E5B9ull;
+    y ^= y >> 27;
+    y *= 0x94D049BB133111EBull;
+    y ^= y >> 31;
+    return y;
+}
+
+// Table for the reduce: word 0 of every row (and of z0) taken through L.
+template <int W>
+__device__ __forceinline__ void load_table_hash_domain(Table<W>& t, const uint64_t* __restrict__ g)
+{
+    uint64_t* d = &t.B[0][0];
+    for (int i = threadIdx.x; i < kTableTotalRows * W; i += blockDim.x) {
+        const uint64_t v = __ldcg(g + i);
+        d[i] = (i % W == 0) ? mix_head(v) : v;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void xor_row(uint64_t (&z)[W], const uint64_t* __restrict__ b)
+{
+#pragma unroll
+    for (int w = 0; w < W; ++w) z[w] ^= b[w];
+}
+
+// z(i) from its definition (seed of a run).
+template <int W>
+__device__ __forceinline__ void seed(const Table<W>& t, uint64_t i, uint64_t (&z)[W])
+{
+    uint64_t g = i ^ (i >> 1);
+#pragma unroll
+    for (int w = 0; w < W; ++w) z[w] = t.z0[w];
+    while (g) {
+        const int k = __ffsll((long long)g) - 1;
+        g &= g - 1;
+        xor_row<W>(z, t.B[k]);
+    }
+}
+
+// Per-thread accumulator of the reduce, fed with solutions whose word 0 is in
+// the L domain (see load_table_hash_domain): sum of hashes and XOR-fold.
+template <int W>
+struct Acc {
+    uint64_t hs;
+    uint64_t fold[W];
+    __device__ __forceinline__ void zero()
+    {
+        hs = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) fold[w] = 0;
+    }
+    __device__ __forceinline__ void consume(const uint64_t (&z)[W])
+    {
+        uint64_t h = mix_tail(z[0]);  // = mix64 of the solution's word 0
+#pragma unroll
+        for (int w = 1; w < W; ++w) h = mix64(h ^ z[w]);
+        hs += h;
+#pragma unroll
+        for (int w = 0; w < W; ++w) fold[w] ^= z[w];
+    }
+    // XOR-fold back in the solution domain (after all XOR reductions).
+    __device__ __forceinline__ uint64_t fold_word(int w) const { return w == 0 ? mix_head_inv(fold[0]) : fold[w]; }
+};
+
+// 2^L consecutive solutions starting at an index that is a multiple of 2^L:
+// the reflected Gray code is (first half, flip bit L-1, second half), so the
+// step between the halves is B_{L-1}, a compile-time register operand.
+template <int W, int U, int L>
+struct GrayBlock {
+    static __device__ __forceinline__ void run(uint64_t (&z)[W], const uint64_t (&Br)[U][W], Acc<W>& acc)
+    {
+        GrayBlock<W, U, L - 1>::run(z, Br, acc);
+        xor_row<W>(z, Br[L - 1]);
+        GrayBlock<W, U, L - 1>::run(z, Br, acc);
+    }
+};
+template <int W, int U>
+struct GrayBlock<W, U, 0> {
+    static __device__ __forceinline__ void run(uint64_t (&z)[W], const uint64_t (&)[U][W], Acc<W>& acc)
+    {
+        acc.consume(z);
+    }
+};
+
+// Walk [i, i + len): consume each solution, step by one row XOR.
+template <int W, int U>
+__device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64_t len, Acc<W>& acc)
+{
+    if (len == 0) return;
+    uint64_t z[W];
+    seed<W>(t, i, z);
+    constexpr uint64_t kBlk = 1ull << U;
+    while (len && (i & (kBlk - 1))) {  // head up to a multiple of 2^U
+        acc.consume(z);
+        --len;
+        ++i;
+        if (len) xor_row<W>(z, t.B[ctz64(i)]);
+    }
+    if (len >= kBlk) {
+        uint64_t Br[U][W];
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+#pragma unroll
+            for (int w = 0; w < W; ++w) Br[k][w] = t.B[k][w];
+        do {
+            GrayBlock<W, U, U>::run(z, Br, acc);
+            len -= kBlk;
+            i += kBlk;
+            if (len) xor_row<W>(z, t.B[ctz64(i)]);  // ctz(i) >= U here
+        } while (len >= kBlk);
+    }
+    while (len) {  // tail
+        acc.consume(z);
+        --len;
+        ++i;
+        if (len) xor_row<W>(z, t.B[ctz64(i)]);
+    }
+}
+
+// Block-wide (count, hsum, fold) reduction; the result is valid in thread 0.
+template <int W>
+__device__ __forceinline__ void block_reduce(uint64_t& cnt, Acc<W>& acc)
+{
+    __shared__ uint64_t s_part[kThreads / 32][2 + W];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        acc.hs += __shfl_xor_sync(0xffffffffu, acc.hs, o);
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc.fold[w] ^= __shfl_xor_sync(0xffffffffu, acc.fold[w], o);
+    }
+    if (lane == 0) {
+        s_part[warp][0] = cnt;
+        s_part[warp][1] = acc.hs;
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_part[warp][2 + w] = acc.fold[w];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        cnt = lane < nw ? s_part[lane][0] : 0;
+        acc.hs = lane < nw ? s_part[lane][1] : 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc.fold[w] = lane < nw ? s_part[lane][2 + w] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            acc.hs += __shfl_xor_sync(0xffffffffu, acc.hs, o);
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc.fold[w] ^= __shfl_xor_sync(0xffffffffu, acc.fold[w], o);
+        }
+    }
+    __syncthreads();  // s_part may be reused by the caller
+}
+
+// Streaming (evict-first) global stores: the solutions are written once and
+// not read back by this kernel.
+
+__device__ __forceinline__ void st_cs_v2(uint64_t* p, uint64_t a, uint64_t b)
+{
+    asm volatile("st.global.cs.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void st_cs(uint64_t* p, uint64_t a)
+{
+    asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
+}
+
+template <int W>
+__device__ __forceinline__ void store_one(uint64_t* p, const uint64_t (&z)[W])
+{
+    if constexpr (W % 2 == 0) {
+#pragma unroll
+        for (int w = 0; w < W; w += 2) st_cs_v2(p + w, z[w], z[w + 1]);
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) st_cs(p + w, z[w]);
+    }
+}
+
+
+}  // namespace hlf

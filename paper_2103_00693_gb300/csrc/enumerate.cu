@@ -26,161 +26,10 @@
 //                        consecutive solutions per step (512 B at W = 1).
 //   sample_kernel        z(i) at arbitrary indices, straight from the formula.
 
-#include "hlf_internal.cuh"
+#include "enum_impl.cuh"
 
 namespace hlf {
 namespace {
-
-constexpr int kThreads = 256;
-
-template <int W>
-struct Table {
-    uint64_t B[kTableRows][W];  // B_0..B_63, zero rows beyond min(r,64), row 64 zero
-    uint64_t z0[W];
-};
-
-template <int W>
-__device__ __forceinline__ void load_table(Table<W>& t, const uint64_t* __restrict__ g)
-{
-    uint64_t* d = &t.B[0][0];
-    for (int i = threadIdx.x; i < kTableTotalRows * W; i += blockDim.x) d[i] = g[i];
-}
-
-template <int W>
-__device__ __forceinline__ void xor_row(uint64_t (&z)[W], const uint64_t* __restrict__ b)
-{
-#pragma unroll
-    for (int w = 0; w < W; ++w) z[w] ^= b[w];
-}
-
-// z(i) from its definition (seed of a run).
-template <int W>
-__device__ __forceinline__ void seed(const Table<W>& t, uint64_t i, uint64_t (&z)[W])
-{
-    uint64_t g = i ^ (i >> 1);
-#pragma unroll
-    for (int w = 0; w < W; ++w) z[w] = t.z0[w];
-    while (g) {
-        const int k = __ffsll((long long)g) - 1;
-        g &= g - 1;
-        xor_row<W>(z, t.B[k]);
-    }
-}
-
-// Per-thread accumulator of the reduce: sum of hashes and XOR-fold.
-template <int W>
-struct Acc {
-    uint64_t hs;
-    uint64_t fold[W];
-    __device__ __forceinline__ void zero()
-    {
-        hs = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) fold[w] = 0;
-    }
-    __device__ __forceinline__ void consume(const uint64_t (&z)[W])
-    {
-        uint64_t h = mix64(z[0]);
-#pragma unroll
-        for (int w = 1; w < W; ++w) h = mix64(h ^ z[w]);
-        hs += h;
-#pragma unroll
-        for (int w = 0; w < W; ++w) fold[w] ^= z[w];
-    }
-};
-
-// 2^L consecutive solutions starting at an index that is a multiple of 2^L:
-// the reflected Gray code is (first half, flip bit L-1, second half), so the
-// step between the halves is B_{L-1}, a compile-time register operand.
-template <int W, int U, int L>
-struct GrayBlock {
-    static __device__ __forceinline__ void run(uint64_t (&z)[W], const uint64_t (&Br)[U][W], Acc<W>& acc)
-    {
-        GrayBlock<W, U, L - 1>::run(z, Br, acc);
-        xor_row<W>(z, Br[L - 1]);
-        GrayBlock<W, U, L - 1>::run(z, Br, acc);
-    }
-};
-template <int W, int U>
-struct GrayBlock<W, U, 0> {
-    static __device__ __forceinline__ void run(uint64_t (&z)[W], const uint64_t (&)[U][W], Acc<W>& acc)
-    {
-        acc.consume(z);
-    }
-};
-
-// Walk [i, i + len): consume each solution, step by one row XOR.
-template <int W, int U>
-__device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64_t len, Acc<W>& acc)
-{
-    if (len == 0) return;
-    uint64_t z[W];
-    seed<W>(t, i, z);
-    constexpr uint64_t kBlk = 1ull << U;
-    while (len && (i & (kBlk - 1))) {  // head up to a multiple of 2^U
-        acc.consume(z);
-        --len;
-        ++i;
-        if (len) xor_row<W>(z, t.B[ctz64(i)]);
-    }
-    if (len >= kBlk) {
-        uint64_t Br[U][W];
-#pragma unroll
-        for (int k = 0; k < U; ++k)
-#pragma unroll
-            for (int w = 0; w < W; ++w) Br[k][w] = t.B[k][w];
-        do {
-            GrayBlock<W, U, U>::run(z, Br, acc);
-            len -= kBlk;
-            i += kBlk;
-            if (len) xor_row<W>(z, t.B[ctz64(i)]);  // ctz(i) >= U here
-        } while (len >= kBlk);
-    }
-    while (len) {  // tail
-        acc.consume(z);
-        --len;
-        ++i;
-        if (len) xor_row<W>(z, t.B[ctz64(i)]);
-    }
-}
-
-// Block-wide (count, hsum, fold) reduction; the result is valid in thread 0.
-template <int W>
-__device__ __forceinline__ void block_reduce(uint64_t& cnt, Acc<W>& acc)
-{
-    __shared__ uint64_t s_part[kThreads / 32][2 + W];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        acc.hs += __shfl_xor_sync(0xffffffffu, acc.hs, o);
-#pragma unroll
-        for (int w = 0; w < W; ++w) acc.fold[w] ^= __shfl_xor_sync(0xffffffffu, acc.fold[w], o);
-    }
-    if (lane == 0) {
-        s_part[warp][0] = cnt;
-        s_part[warp][1] = acc.hs;
-#pragma unroll
-        for (int w = 0; w < W; ++w) s_part[warp][2 + w] = acc.fold[w];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        cnt = lane < nw ? s_part[lane][0] : 0;
-        acc.hs = lane < nw ? s_part[lane][1] : 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) acc.fold[w] = lane < nw ? s_part[lane][2 + w] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            acc.hs += __shfl_xor_sync(0xffffffffu, acc.hs, o);
-#pragma unroll
-            for (int w = 0; w < W; ++w) acc.fold[w] ^= __shfl_xor_sync(0xffffffffu, acc.fold[w], o);
-        }
-    }
-    __syncthreads();  // s_part may be reused by the caller
-}
 
 template <int W, int U>
 __global__ void __launch_bounds__(kThreads) reduce_kernel(const uint64_t* __restrict__ table, uint64_t offset,
@@ -188,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const uint64_t* __rest
                                                           uint64_t threads_used, hlf_reduce* __restrict__ out)
 {
     __shared__ Table<W> t;
-    load_table<W>(t, table);
+    load_table_hash_domain<W>(t, table);
     __syncthreads();
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     Acc<W> acc;
@@ -207,10 +56,10 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const uint64_t* __rest
         atomicAdd(reinterpret_cast<unsigned long long*>(&out->count), (unsigned long long)cnt);
         atomicAdd(reinterpret_cast<unsigned long long*>(&out->hsum), (unsigned long long)acc.hs);
 #pragma unroll
-        for (int w = 0; w < W; ++w)
-            if (acc.fold[w])
-                atomicXor(reinterpret_cast<unsigned long long*>(&out->xor_fold[w]),
-                          (unsigned long long)acc.fold[w]);
+        for (int w = 0; w < W; ++w) {
+            const uint64_t f = acc.fold_word(w);
+            if (f) atomicXor(reinterpret_cast<unsigned long long*>(&out->xor_fold[w]), (unsigned long long)f);
+        }
     }
 }
 
@@ -220,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) reduce_chunks_kernel(const uint64_t*
                                                                  uint64_t n_chunks, hlf_reduce* __restrict__ out)
 {
     __shared__ Table<W> t;
-    load_table<W>(t, table);
+    load_table_hash_domain<W>(t, table);
     __syncthreads();
     const uint64_t per_thread = (chunk + blockDim.x - 1) / blockDim.x;
     for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
@@ -239,31 +88,8 @@ __global__ void __launch_bounds__(kThreads) reduce_chunks_kernel(const uint64_t*
             r.count = cnt;
             r.hsum = acc.hs;
 #pragma unroll
-            for (int w = 0; w < HLF_MAX_W; ++w) r.xor_fold[w] = w < W ? acc.fold[w] : 0ull;
+            for (int w = 0; w < HLF_MAX_W; ++w) r.xor_fold[w] = w < W ? acc.fold_word(w) : 0ull;
         }
-    }
-}
-
-// ------------------------------------------------------------------ store
-
-__device__ __forceinline__ void st_cs_v2(uint64_t* p, uint64_t a, uint64_t b)
-{
-    asm volatile("st.global.cs.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
-}
-__device__ __forceinline__ void st_cs(uint64_t* p, uint64_t a)
-{
-    asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
-}
-
-template <int W>
-__device__ __forceinline__ void store_one(uint64_t* p, const uint64_t (&z)[W])
-{
-    if constexpr (W % 2 == 0) {
-#pragma unroll
-        for (int w = 0; w < W; w += 2) st_cs_v2(p + w, z[w], z[w + 1]);
-    } else {
-#pragma unroll
-        for (int w = 0; w < W; ++w) st_cs(p + w, z[w]);
     }
 }
 
@@ -364,7 +190,15 @@ hlf_status launch_reduce_w(const uint64_t* table, uint64_t offset, uint64_t coun
                            cudaStream_t s)
 {
     constexpr int U = unroll_for(W);
-    const uint64_t max_threads = (uint64_t)sm_count() * 8 * kThreads;
+    // one wave: as many CTAs as fit on every SM at once
+    static int fit[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && fit[dev] == 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit[dev], reduce_kernel<W, U>, kThreads, 0) != cudaSuccess)
+        return HLF_ERR_CUDA;
+    const int per_sm = (dev < 64 && fit[dev] > 0) ? fit[dev] : 1;
+    const uint64_t max_threads = (uint64_t)sm_count() * per_sm * kThreads;
     const uint64_t min_run = 2048;  // amortises the <= 64-row seed
     uint64_t threads = (count + min_run - 1) / min_run;
     if (threads > max_threads) threads = max_threads;

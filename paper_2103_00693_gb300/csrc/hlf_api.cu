@@ -85,6 +85,19 @@ hlf_status after_launch(hlf_handle* h, hlf_status st, cudaStream_t s)
 
 namespace hlf {
 
+hlf_status handle_enum_view(hlf_handle* h, const uint64_t** table, int32_t* r, int32_t* W)
+{
+    if (!h) return HLF_ERR_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return HLF_ERR_CUDA;
+    hlf_status st = ensure_rank(h);
+    if (st != HLF_OK) return st;
+    *table = h->table;
+    *r = h->r;
+    *W = h->W;
+    return HLF_OK;
+}
+
 int sm_count()
 {
     static int cache[64] = {0};

@@ -22,6 +22,7 @@ from . import build as _build
 
 MAX_N = 1024
 MAX_W = 16
+BATCH_MAX_N = 256
 REDUCE_WORDS = 2 + MAX_W  # hlf_reduce: count, hsum, xor_fold[16]
 
 STATUS = {
@@ -29,6 +30,8 @@ STATUS = {
     4: "HLF_ERR_PADDING", 5: "HLF_ERR_RANGE", 6: "HLF_ERR_NOMEM", 7: "HLF_ERR_TIMEOUT",
     8: "HLF_ERR_CUDA", 9: "HLF_ERR_INTERNAL",
 }
+
+STATUS_CODES = {v: k for k, v in STATUS.items()}
 
 # Every entry point of include/hlf.h, with its ctypes signature.
 _vp = ctypes.c_void_p
@@ -47,6 +50,16 @@ SIGNATURES = {
     "hlf_enumerate_reduce_chunks": (ctypes.c_int, [_vp, _u64, _u64, _u64, _vp, _vp]),
     "hlf_sample": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp]),
     "hlf_destroy": (ctypes.c_int, [_vp]),
+    "hlf_many_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp)]),
+    "hlf_enumerate_store_many": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "hlf_many_destroy": (ctypes.c_int, [_vp]),
+    "hlf_batch_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp)]),
+    "hlf_batch_set_tiles": (ctypes.c_int, [_vp, _i32, _u64]),
+    "hlf_batch_set_spin_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+    "hlf_batch_factor_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _u64, _vp, _vp, _vp]),
+    "hlf_batch_set_debug": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+    "hlf_batch_get_status": (ctypes.c_int, [_vp]),
+    "hlf_batch_destroy": (ctypes.c_int, [_vp]),
 }
 
 
@@ -205,6 +218,61 @@ def hlf_sample(h: int, idx_dev, m: int, out_dev, stream=None):
 
 def hlf_destroy(h: int):
     _check(load().hlf_destroy(h), "hlf_destroy")
+
+
+def hlf_many_create(max_windows: int) -> int:
+    m = _vp()
+    _check(load().hlf_many_create(max_windows, ctypes.byref(m)), "hlf_many_create")
+    return m.value
+
+
+def hlf_enumerate_store_many(m: int, handles, offsets, counts, outs, stream=None):
+    """handles: list of handle values; offsets/counts: lists of ints; outs:
+    list of CUDA tensors (each [count_j, W_j] 64-bit)."""
+    k = len(handles)
+    hs = (_vp * max(k, 1))(*handles)
+    offs = (_u64 * max(k, 1))(*offsets)
+    cnts = (_u64 * max(k, 1))(*counts)
+    outp = (_vp * max(k, 1))(*[o.data_ptr() for o in outs])
+    _check(load().hlf_enumerate_store_many(m, hs, offs, cnts, outp, k, _stream_ptr(stream)),
+           "hlf_enumerate_store_many")
+
+
+def hlf_many_destroy(m: int):
+    _check(load().hlf_many_destroy(m), "hlf_many_destroy")
+
+
+def hlf_batch_create(max_instances: int) -> int:
+    b = _vp()
+    _check(load().hlf_batch_create(max_instances, ctypes.byref(b)), "hlf_batch_create")
+    return b.value
+
+
+def hlf_batch_set_tiles(b: int, ctas_per_sm: int, chunk: int):
+    _check(load().hlf_batch_set_tiles(b, ctas_per_sm, chunk), "hlf_batch_set_tiles")
+
+
+def hlf_batch_set_spin_limit(b: int, polls: int):
+    _check(load().hlf_batch_set_spin_limit(b, polls), "hlf_batch_set_spin_limit")
+
+
+def hlf_batch_factor_reduce(b: int, A_dev, word_off_dev, n_dev, count: int, cap: int, r_dev, red_dev,
+                            stream=None):
+    _check(load().hlf_batch_factor_reduce(b, _ptr(A_dev), _ptr(word_off_dev), _ptr(n_dev), count, cap,
+                                          _ptr(r_dev), _ptr(red_dev), _stream_ptr(stream)),
+           "hlf_batch_factor_reduce")
+
+
+def hlf_batch_set_debug(b: int, flags: int):
+    _check(load().hlf_batch_set_debug(b, flags), "hlf_batch_set_debug")
+
+
+def hlf_batch_get_status(b: int) -> int:
+    return int(load().hlf_batch_get_status(b))
+
+
+def hlf_batch_destroy(b: int):
+    _check(load().hlf_batch_destroy(b), "hlf_batch_destroy")
 
 
 # ------------------------------------------------------------ convenience layer

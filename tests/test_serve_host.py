@@ -1,0 +1,43 @@
+"""Host-side logic of the request loop (no GPU): window placement inside the
+index space, memory accounting, statistics."""
+
+import numpy as np
+
+from paper_2103_00693_gb300 import serve
+from synth import workloads as wl
+
+
+def test_window_of_inside_space():
+    rng = np.random.default_rng(0)
+    for _ in range(2000):
+        r = int(rng.integers(0, 200))
+        want = int(rng.integers(1, 1 << 24))
+        u = int(rng.integers(0, 1 << 63))
+        off, cnt = serve.window_of(r, want, u)
+        space = 1 << min(r, 64)
+        assert cnt == min(want, space)
+        assert 0 <= off and off + cnt <= space
+
+
+def test_window_of_small_spaces():
+    assert serve.window_of(0, 100, 12345) == (0, 1)
+    assert serve.window_of(3, 100, 7) == (0, 8)
+    assert serve.window_of(3, 5, 7) == (7 % 4, 5)
+
+
+def test_handle_bytes_grows_with_n():
+    assert serve.handle_bytes(9) < serve.handle_bytes(64) < serve.handle_bytes(1024)
+
+
+def test_stats_summary():
+    st = serve.Stats(n_requests=3, solutions=300, bytes_out=2400, makespan_s=2.0,
+                     latencies_ms=[1.0, 2.0, 3.0], busy_s=1.0, ticks=2, launches=2)
+    s = st.summary()
+    assert s["solutions_per_s"] == 150.0 and s["p50_ms"] == 2.0 and s["busy_frac"] == 0.5
+
+
+def test_stream_workload_shape():
+    reqs = wl.stream(50, 1000.0)
+    assert len(reqs) == 50
+    assert all(9 <= q["A"].shape[0] <= 1024 for q in reqs)
+    assert all((1 << 10) <= q["want"] <= (1 << 24) for q in reqs)

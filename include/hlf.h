@@ -247,6 +247,39 @@ hlf_status hlf_batch_get_status(hlf_batch* b);
 /* Frees the plan (waits for its last launch). NULL is accepted. */
 hlf_status hlf_batch_destroy(hlf_batch* b);
 
+/*
+ * hlf_batch_factor_reduce without allocating anything (the paper has no
+ * counterpart; this exists for callers, not for the method).
+ *
+ * Some callers cannot call cudaMalloc when they need this work done: a host
+ * application that owns all device memory and hands a plugin only its input
+ * and output pointers; a framework whose memory pool has already reserved the
+ * device; a latency-critical loop that must not risk the device-wide
+ * synchronisation cudaMalloc and cudaFree can cause. This entry point needs no
+ * plan: its workspace is a fixed array in the library's device image, sized
+ * for HLF_BATCH_NOALLOC_MAX matrices (about 2.1 MiB), which every GPU that
+ * loads the library holds until the process exits. It never calls cudaMalloc,
+ * cudaFree or any allocating routine.
+ *
+ * Arguments, layout and results are those of hlf_batch_factor_reduce with the
+ * default launch shape (CTAs per SM: as many as fit; 2^16 solutions per work
+ * item; 2^23 polls per wait). count > HLF_BATCH_NOALLOC_MAX returns
+ * HLF_ERR_SIZE and enqueues nothing. A bounded wait that runs out cannot be
+ * reported separately here; it shows as red_dev[b].count below
+ * min(2^r_b, cap).
+ *
+ * The first call on each device looks up the workspace's device address
+ * (with that device current); make that first call before any stream
+ * capture. Every call shares the one workspace, and each call clears what must
+ * start at zero, so calls whose work overlaps on the GPU (on different streams,
+ * or from different host threads) race and give wrong results: issue them in
+ * one stream order.
+ */
+#define HLF_BATCH_NOALLOC_MAX 1024
+hlf_status hlf_batch_factor_reduce_noalloc(const uint64_t* A_dev, const int64_t* word_off_dev,
+                                           const int32_t* n_dev, int32_t count, uint64_t cap, int32_t* r_dev,
+                                           hlf_reduce* red_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

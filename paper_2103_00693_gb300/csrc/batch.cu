@@ -15,6 +15,7 @@
 // Every wait is bounded: after spin_limit polls the chunk is skipped and
 // HLF_ERR_TIMEOUT is recorded in the batch status word.
 
+#include <mutex>
 #include <new>
 
 #include "enum_impl.cuh"
@@ -179,6 +180,31 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BatchArgs a)
 }  // namespace
 }  // namespace hlf
 
+// ---------------------------------------------------------------------------
+// Scratch for hlf_batch_factor_reduce_noalloc: a file-scope device array, so
+// that entry point never allocates. It holds the same workspace a plan holds,
+// for up to HLF_BATCH_NOALLOC_MAX matrices. Host code must not use the
+// array's name as a device address: the address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+namespace hlf {
+namespace {
+
+struct NoAllocScratch {
+    uint64_t tables[(size_t)HLF_BATCH_NOALLOC_MAX * kTableSlot];
+    int32_t info[2 * HLF_BATCH_NOALLOC_MAX];
+    int32_t ready[HLF_BATCH_NOALLOC_MAX];
+    uint32_t counter;
+    int32_t status;
+};
+
+}  // namespace
+}  // namespace hlf
+
+static __device__ __align__(256) unsigned char g_batch_noalloc_scratch[sizeof(hlf::NoAllocScratch)];
+
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_addr[64] = {nullptr};
+
 struct hlf_batch {
     int device = 0;
     int32_t max_instances = 0;
@@ -335,6 +361,73 @@ hlf_status hlf_batch_get_status(hlf_batch* b)
             return HLF_ERR_CUDA;
     }
     return (hlf_status)st;
+}
+
+hlf_status hlf_batch_factor_reduce_noalloc(const uint64_t* A_dev, const int64_t* word_off_dev,
+                                           const int32_t* n_dev, int32_t count, uint64_t cap, int32_t* r_dev,
+                                           hlf_reduce* red_dev, void* stream)
+{
+    if (count < 0 || cap == 0) return HLF_ERR_ARG;
+    if (count > HLF_BATCH_NOALLOC_MAX) return HLF_ERR_SIZE;
+    if (count == 0) return HLF_OK;
+    if (!A_dev || !word_off_dev || !n_dev || !r_dev || !red_dev) return HLF_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HLF_ERR_CUDA;
+    if (dev < 0 || dev >= 64) return HLF_ERR_ARG;
+    unsigned char* base = nullptr;
+    {
+        // First call on this device: find the scratch array's device address
+        // (the device is current here) and allow the kernel its shared memory.
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_batch_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return HLF_ERR_CUDA;
+            }
+            if (cudaFuncSetAttribute(hlf::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)hlf::batch_smem_bytes()) != cudaSuccess) {
+                cudaGetLastError();
+                return HLF_ERR_CUDA;
+            }
+            g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+        }
+        base = g_noalloc_addr[dev];
+    }
+    hlf::NoAllocScratch* sc = reinterpret_cast<hlf::NoAllocScratch*>(base);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    hlf::BatchArgs a{};
+    a.A = A_dev;
+    a.word_off = word_off_dev;
+    a.n = n_dev;
+    a.B = count;
+    a.cap = cap;
+    a.chunk = 1ull << 16;
+    const uint64_t cpi = (cap + a.chunk - 1) / a.chunk;
+    if (cpi > (1u << 20) || (uint64_t)count * (cpi + 1) > 0xffffffffull) return HLF_ERR_RANGE;
+    a.chunks_per_inst = (uint32_t)cpi;
+    a.r_out = r_dev;
+    a.red_out = red_dev;
+    a.tables = sc->tables;
+    a.info = sc->info;
+    a.ready = sc->ready;
+    a.counter = &sc->counter;
+    a.status = &sc->status;
+    a.spin_limit = 1u << 23;
+    a.first_item = 0;
+    // The array keeps the previous call's contents: clear the queue counter,
+    // the status word and this call's ready flags; the results are overwritten.
+    if (cudaMemsetAsync(&sc->counter, 0, sizeof(uint32_t) + sizeof(int32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(sc->ready, 0, sizeof(int32_t) * (size_t)count, s) != cudaSuccess ||
+        cudaMemsetAsync(red_dev, 0, sizeof(hlf_reduce) * (size_t)count, s) != cudaSuccess)
+        return HLF_ERR_CUDA;
+    const size_t smem = hlf::batch_smem_bytes();
+    int fit = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, hlf::batch_kernel, hlf::kThreads, smem) != cudaSuccess ||
+        fit < 1)
+        return HLF_ERR_CUDA;
+    hlf::batch_kernel<<<hlf::sm_count() * fit, hlf::kThreads, smem, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
 hlf_status hlf_batch_destroy(hlf_batch* b)

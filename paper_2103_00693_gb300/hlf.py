@@ -60,6 +60,7 @@ SIGNATURES = {
     "hlf_batch_set_debug": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "hlf_batch_get_status": (ctypes.c_int, [_vp]),
     "hlf_batch_destroy": (ctypes.c_int, [_vp]),
+    "hlf_batch_factor_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i32, _u64, _vp, _vp, _vp]),
 }
 
 
@@ -273,6 +274,20 @@ def hlf_batch_get_status(b: int) -> int:
 
 def hlf_batch_destroy(b: int):
     _check(load().hlf_batch_destroy(b), "hlf_batch_destroy")
+
+
+BATCH_NOALLOC_MAX = 1024
+
+
+def hlf_batch_factor_reduce_noalloc(A_dev, word_off_dev, n_dev, count: int, cap: int, r_dev, red_dev,
+                                    stream=None):
+    """hlf_batch_factor_reduce without a plan and without any allocation in
+    the library: for callers that cannot allocate device memory when they
+    call (see include/hlf.h). At most BATCH_NOALLOC_MAX matrices per call;
+    calls must not overlap on the GPU."""
+    _check(load().hlf_batch_factor_reduce_noalloc(_ptr(A_dev), _ptr(word_off_dev), _ptr(n_dev), count, cap,
+                                                  _ptr(r_dev), _ptr(red_dev), _stream_ptr(stream)),
+           "hlf_batch_factor_reduce_noalloc")
 
 
 # ------------------------------------------------------------ convenience layer

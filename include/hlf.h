@@ -95,7 +95,10 @@ int32_t hlf_device_count(void);
  *         ends (i.e. in stream order), not retained.
  * n:      1 .. HLF_MAX_N.
  * stream: cudaStream_t the kernel is launched on.
- * *h:     receives a new handle (library-owned; free with hlf_destroy).
+ * *h:     receives a new handle (library-owned; free with hlf_destroy). Its
+ *         few device buffers come from the device's stream-ordered memory
+ *         pool (cudaMallocAsync on `stream`), so creating and destroying
+ *         handles never synchronises the device.
  * Computes r, P, B_0..B_{r-1} and z0 on the device. Asynchronous: symmetry
  * and padding faults surface on the first synchronising call on *h.
  * Returns HLF_ERR_SIZE for bad n, HLF_ERR_ARG for null pointers,
@@ -157,8 +160,10 @@ hlf_status hlf_enumerate_reduce_chunks(hlf_handle* h, uint64_t offset, uint64_t 
 hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64_t* out_dev,
                       void* stream);
 
-/* Frees the handle and its device buffers (waits for its work first).
- * NULL is accepted. */
+/* Frees the handle. Its device buffers (allocated stream-ordered on the
+ * stream given to hlf_factor) are released in stream order after the last
+ * work enqueued through the handle; the host does not wait. NULL is
+ * accepted. */
 hlf_status hlf_destroy(hlf_handle* h);
 
 /* ------------------------------------------------------------ many windows

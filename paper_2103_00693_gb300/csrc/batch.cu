@@ -75,13 +75,13 @@ template <int W>
 __device__ void batch_factor(const BatchArgs& a, int b, int n, unsigned char* smem)
 {
     FactorOut o{nullptr, nullptr, a.tables + (size_t)b * kTableSlot, a.info + 2 * b};
-    factor_block<W, kBatchMaxN>(a.A + a.word_off[b], n, o, smem);
+    factor_block<W, 1, kBatchMaxN>(a.A + a.word_off[b], n, o, smem);
 }
 
 template <int W>
 __device__ void batch_chunk(const BatchArgs& a, int b, uint64_t first, uint64_t len, unsigned char* smem)
 {
-    constexpr int U = W <= 2 ? 4 : 3;
+    constexpr int U = unroll_for(W);
     Table<W>& t = *reinterpret_cast<Table<W>*>(smem);
     load_table_hash_domain<W>(t, a.tables + (size_t)b * kTableSlot);
     __syncthreads();
@@ -107,7 +107,7 @@ __device__ void batch_chunk(const BatchArgs& a, int b, uint64_t first, uint64_t 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) batch_kernel(BatchArgs a)
+__global__ void __launch_bounds__(kThreads, 4) batch_kernel(BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_item;

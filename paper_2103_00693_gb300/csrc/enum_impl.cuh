@@ -11,6 +11,12 @@ namespace hlf {
 
 constexpr int kThreads = 256;
 
+// Solutions unrolled per block (2^U): enough independent hash chains per
+// thread at W = 1; beyond that each solution is already 24W - 4 operations,
+// and deeper unrolling only costs registers (occupancy).
+constexpr int unroll_for(int W) { return W == 1 ? 4 : (W == 2 ? 2 : 1); }
+constexpr int min_ctas_for(int W) { return W == 1 ? 6 : (W <= 4 ? 4 : 2); }
+
 template <int W>
 struct Table {
     uint64_t B[kTableRows][W];  // B_0..B_63, zero rows beyond min(r,64), row 64 zero
@@ -101,22 +107,21 @@ struct Acc {
 
 // 2^L consecutive solutions starting at an index that is a multiple of 2^L:
 // the reflected Gray code is (first half, flip bit L-1, second half), so the
-// step between the halves is B_{L-1}, a compile-time register operand.
-template <int W, int U, int L>
+// step between the halves is row L-1, at a compile-time index. `Rows` is a
+// register array (W = 1) or the shared-memory table (W > 1, where register
+// copies of U rows of W words would cost more occupancy than they save).
+template <int W, int L, typename Rows>
 struct GrayBlock {
-    static __device__ __forceinline__ void run(uint64_t (&z)[W], const uint64_t (&Br)[U][W], Acc<W>& acc)
+    static __device__ __forceinline__ void run(uint64_t (&z)[W], const Rows& Br, Acc<W>& acc)
     {
-        GrayBlock<W, U, L - 1>::run(z, Br, acc);
+        GrayBlock<W, L - 1, Rows>::run(z, Br, acc);
         xor_row<W>(z, Br[L - 1]);
-        GrayBlock<W, U, L - 1>::run(z, Br, acc);
+        GrayBlock<W, L - 1, Rows>::run(z, Br, acc);
     }
 };
-template <int W, int U>
-struct GrayBlock<W, U, 0> {
-    static __device__ __forceinline__ void run(uint64_t (&z)[W], const uint64_t (&)[U][W], Acc<W>& acc)
-    {
-        acc.consume(z);
-    }
+template <int W, typename Rows>
+struct GrayBlock<W, 0, Rows> {
+    static __device__ __forceinline__ void run(uint64_t (&z)[W], const Rows&, Acc<W>& acc) { acc.consume(z); }
 };
 
 // Walk [i, i + len): consume each solution, step by one row XOR.
@@ -134,17 +139,24 @@ __device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64
         if (len) xor_row<W>(z, t.B[ctz64(i)]);
     }
     if (len >= kBlk) {
-        uint64_t Br[U][W];
+        if constexpr (W == 1) {
+            uint64_t Br[U][W];
 #pragma unroll
-        for (int k = 0; k < U; ++k)
-#pragma unroll
-            for (int w = 0; w < W; ++w) Br[k][w] = t.B[k][w];
-        do {
-            GrayBlock<W, U, U>::run(z, Br, acc);
-            len -= kBlk;
-            i += kBlk;
-            if (len) xor_row<W>(z, t.B[ctz64(i)]);  // ctz(i) >= U here
-        } while (len >= kBlk);
+            for (int k = 0; k < U; ++k) Br[k][0] = t.B[k][0];
+            do {
+                GrayBlock<W, U, uint64_t[U][W]>::run(z, Br, acc);
+                len -= kBlk;
+                i += kBlk;
+                if (len) xor_row<W>(z, t.B[ctz64(i)]);  // ctz(i) >= U here
+            } while (len >= kBlk);
+        } else {
+            do {
+                GrayBlock<W, U, uint64_t[kTableRows][W]>::run(z, t.B, acc);
+                len -= kBlk;
+                i += kBlk;
+                if (len) xor_row<W>(z, t.B[ctz64(i)]);
+            } while (len >= kBlk);
+        }
     }
     while (len) {  // tail
         acc.consume(z);

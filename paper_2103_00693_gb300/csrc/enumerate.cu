@@ -31,8 +31,10 @@
 namespace hlf {
 namespace {
 
+
+
 template <int W, int U>
-__global__ void __launch_bounds__(kThreads) reduce_kernel(const uint64_t* __restrict__ table, uint64_t offset,
+__global__ void __launch_bounds__(kThreads, min_ctas_for(W)) reduce_kernel(const uint64_t* __restrict__ table, uint64_t offset,
                                                           uint64_t count, uint64_t per_thread,
                                                           uint64_t threads_used, hlf_reduce* __restrict__ out)
 {
@@ -183,7 +185,6 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const uint64_t* __rest
 
 // ------------------------------------------------------------- launchers
 
-constexpr int unroll_for(int W) { return W <= 2 ? 4 : (W <= 8 ? 3 : 2); }
 
 template <int W>
 hlf_status launch_reduce_w(const uint64_t* table, uint64_t offset, uint64_t count, hlf_reduce* out,

@@ -1,5 +1,7 @@
-// Stage 1 for one matrix: one CTA of round_up(n, 32) threads runs
-// factor_block (factor_impl.cuh) with the rows of A in registers.
+// Stage 1 for one matrix: one CTA runs factor_block (factor_impl.cuh) with
+// the rows of A in registers: one row per thread up to n = 512, two rows per
+// thread above (at most 512 threads, so up to 128 registers each and no
+// spilling of the 16-word rows of n = 1024).
 
 #include "factor_impl.cuh"
 
@@ -7,16 +9,20 @@ namespace hlf {
 namespace {
 
 template <int W>
-__global__ void __launch_bounds__(1024) factor_kernel(const uint64_t* __restrict__ A, int n, FactorOut o)
+constexpr int rows_per_thread() { return W <= 8 ? 1 : 2; }
+
+template <int W>
+__global__ void __launch_bounds__(512) factor_kernel(const uint64_t* __restrict__ A, int n, FactorOut o)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    factor_block<W, HLF_MAX_N>(A, n, o, smem);
+    factor_block<W, rows_per_thread<W>(), HLF_MAX_N>(A, n, o, smem);
 }
 
 template <int W>
 hlf_status launch_factor_w(const uint64_t* A, int n, const FactorOut& o, cudaStream_t s)
 {
-    const int threads = ((n + 31) / 32) * 32;
+    constexpr int R = rows_per_thread<W>();
+    const int threads = ((n + R - 1) / R + 31) / 32 * 32;
     const size_t smem = factor_smem_bytes<W, HLF_MAX_N>(n);
     static bool attr_set[64] = {false};
     int dev = 0;

@@ -1,10 +1,11 @@
 // Stage 1 of the two-stage scheme as a block-level device function: the CLA
 // module of Section 2 (Fig. 1(b)), steps (1)-(4), for one matrix per CTA.
 //
-//   (1) Gauss-Jordan elimination of A over GF(2). Thread i owns row i of A in
-//       registers (W uint64 words). For each column c, left to right, the
-//       candidates are the rows not yet used as a pivot that have bit c set;
-//       a warp ballot plus a min over warps picks the lowest such row p. Row p
+//   (1) Gauss-Jordan elimination of A over GF(2). Each thread owns R rows of
+//       A in registers (W uint64 words each). For each column c, left to
+//       right, the candidates are the rows not yet used as a pivot that have
+//       bit c set; a min over each warp and then over the warps picks the
+//       lowest such row p. Row p
 //       is broadcast through shared memory and every other row with bit c set
 //       XORs it in (rows above and below: Gauss-Jordan, so the result is the
 //       unique reduced row echelon form). Rows are never swapped; the pivot
@@ -41,11 +42,12 @@ constexpr size_t factor_smem_bytes(int n)
 }
 
 // Factor the n x n matrix A ([n][W] words, global) with the whole CTA.
-// Requires blockDim.x >= n, blockDim.x a multiple of 32, n <= MAXN.
-// `smem` points to factor_smem_bytes<W, MAXN>(n) bytes of shared memory.
-// Writes o.table (always), o.basis and o.piv (when non-null) and
-// o.info[0] = status, o.info[1] = r (or -1 on a fault). Returns r, or -1.
-template <int W, int MAXN>
+// Thread t owns the R rows t, t + blockDim.x, ... in registers. Requires
+// R * blockDim.x >= n, blockDim.x a multiple of 32, n <= MAXN. `smem` points
+// to factor_smem_bytes<W, MAXN>(n) bytes of shared memory. Writes o.table
+// (always), o.basis and o.piv (when non-null) and o.info[0] = status,
+// o.info[1] = r (or -1 on a fault). Returns r, or -1.
+template <int W, int R, int MAXN>
 __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorOut& o, unsigned char* smem)
 {
     constexpr int kNone = 0x7fffffff;
@@ -53,40 +55,47 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
     uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem + sizeof(FactorSmem<W, MAXN>));  // [n][W]
 
     const int tid = threadIdx.x;
+    const int bs = blockDim.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const int nwarps = blockDim.x >> 5;
+    const int nwarps = bs >> 5;
 
-    uint64_t row[W];
+    uint64_t row[R][W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) row[w] = tid < n ? A[(size_t)tid * W + w] : 0ull;
-    if (tid < n) {
+    for (int j = 0; j < R; ++j) {
+        const int i = tid + j * bs;
 #pragma unroll
-        for (int w = 0; w < W; ++w) s_rows[tid * W + w] = row[w];
+        for (int w = 0; w < W; ++w) row[j][w] = i < n ? A[(size_t)i * W + w] : 0ull;
+        if (i < n) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) s_rows[i * W + w] = row[j][w];
+        }
     }
     if (tid == 0) sm.err = 0;
     if (tid < W) sm.z0[tid] = 0;
-    for (int i = tid; i < MAXN / 32; i += blockDim.x) sm.pivmask[i] = 0;
+    for (int i = tid; i < MAXN / 32; i += bs) sm.pivmask[i] = 0;
     __syncthreads();
 
     // ---- input checks: padding, then symmetry (bit j of row i == bit i of row j)
     int bad = 0;
-    if (tid < n) {
-        const int tail = n & 63;
-        if (tail && (row[W - 1] >> tail)) bad = HLF_ERR_PADDING;
-        const int wi = tid >> 6;
-        const int bi = tid & 63;
-        if (!bad) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                uint64_t t = 0;
-                for (int b = 0; b < 64; ++b) {
-                    const int j = (w << 6) + b;
-                    if (j >= n) break;
-                    t |= ((s_rows[j * W + wi] >> bi) & 1ull) << b;
-                }
-                if (t != row[w]) bad = HLF_ERR_NOT_SYMMETRIC;
+    for (int j = 0; j < R; ++j) {
+        const int i = tid + j * bs;
+        if (i >= n) continue;
+        const int tail = n & 63;
+        if (tail && (row[j][W - 1] >> tail)) bad = HLF_ERR_PADDING;
+        const int wi = i >> 6;
+        const int bi = i & 63;
+        if (bad) continue;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t t = 0;
+            for (int b = 0; b < 64; ++b) {
+                const int c = (w << 6) + b;
+                if (c >= n) break;
+                t |= ((s_rows[c * W + wi] >> bi) & 1ull) << b;
             }
+            if (t != row[j][w]) bad = HLF_ERR_NOT_SYMMETRIC;
         }
     }
     if (bad) atomicMax(&sm.err, bad);
@@ -102,8 +111,13 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
     }
 
     // ---- (1) Gauss-Jordan elimination
-    bool used = false;
-    int my_k = -1;
+    bool used[R];
+    int my_k[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        used[j] = false;
+        my_k[j] = -1;
+    }
     int rank = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -111,24 +125,35 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
             const int c = (w << 6) + b;
             if (c >= n) break;
             const int buf = c & 1;
-            const bool cand = tid < n && !used && ((row[w] >> b) & 1ull);
-            const unsigned m = __ballot_sync(0xffffffffu, cand);
-            if (lane == 0) sm.first[buf][warp] = m ? (warp << 5) + __ffs(m) - 1 : kNone;
+            int cand = kNone;  // this thread's lowest unused row with bit c
+#pragma unroll
+            for (int j = R - 1; j >= 0; --j)
+                if (tid + j * bs < n && !used[j] && ((row[j][w] >> b) & 1ull)) cand = tid + j * bs;
+            cand = __reduce_min_sync(0xffffffffu, cand);
+            if (lane == 0) sm.first[buf][warp] = cand;
             __syncthreads();
             int p = lane < nwarps ? sm.first[buf][lane] : kNone;
             p = __reduce_min_sync(0xffffffffu, p);
             if (p == kNone) continue;  // no pivot in column c (uniform)
-            if (tid == p) {
+            if (tid == p % bs) {
+                const int pj = p / bs;
 #pragma unroll
-                for (int v = 0; v < W; ++v) sm.prow[buf][v] = row[v];
-                used = true;
-                my_k = rank;
+                for (int j = 0; j < R; ++j) {
+                    if (j != pj) continue;
+#pragma unroll
+                    for (int v = 0; v < W; ++v) sm.prow[buf][v] = row[j][v];
+                    used[j] = true;
+                    my_k[j] = rank;
+                }
             }
             if (tid == 0) sm.pivcol[rank] = c;
             __syncthreads();
-            if (tid != p && ((row[w] >> b) & 1ull)) {
 #pragma unroll
-                for (int v = 0; v < W; ++v) row[v] ^= sm.prow[buf][v];
+            for (int j = 0; j < R; ++j) {
+                if (tid + j * bs != p && ((row[j][w] >> b) & 1ull)) {
+#pragma unroll
+                    for (int v = 0; v < W; ++v) row[j][v] ^= sm.prow[buf][v];
+                }
             }
             ++rank;
         }
@@ -138,16 +163,19 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
     __syncthreads();  // all reads of the input rows in s_rows are done
 
     // ---- outputs of step (1): B_k in pivot order, pivots, enumeration table
-    if (used) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (!used[j]) continue;
+        const int k = my_k[j];
 #pragma unroll
         for (int v = 0; v < W; ++v) {
-            s_rows[my_k * W + v] = row[v];
-            if (o.basis) o.basis[(size_t)my_k * W + v] = row[v];
-            if (my_k < HLF_MAX_VARYING) o.table[my_k * W + v] = row[v];
+            s_rows[k * W + v] = row[j][v];
+            if (o.basis) o.basis[(size_t)k * W + v] = row[j][v];
+            if (k < HLF_MAX_VARYING) o.table[k * W + v] = row[j][v];
         }
     }
-    for (int i = nb * W + tid; i < kTableRows * W; i += blockDim.x) o.table[i] = 0ull;
-    for (int k = tid; k < r; k += blockDim.x) {
+    for (int i = nb * W + tid; i < kTableRows * W; i += bs) o.table[i] = 0ull;
+    for (int k = tid; k < r; k += bs) {
         const int c = sm.pivcol[k];
         if (o.piv) o.piv[k] = c;
         atomicOr(&sm.pivmask[c >> 5], 1u << (c & 31));

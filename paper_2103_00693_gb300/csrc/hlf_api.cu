@@ -98,6 +98,21 @@ hlf_status handle_enum_view(hlf_handle* h, const uint64_t** table, int32_t* r, i
     return HLF_OK;
 }
 
+void keep_pool_memory()
+{
+    // Keep freed blocks in the device's default pool instead of returning
+    // them to the driver at every synchronisation (once per device).
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = 1ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[dev] = true;
+}
+
 int sm_count()
 {
     static int cache[64] = {0};
@@ -157,7 +172,10 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
     const size_t off_table = round_up(off_piv + sizeof(int32_t) * n, 256);
     const size_t off_basis = round_up(off_table + sizeof(uint64_t) * hlf::kTableTotalRows * h->W, 256);
     const size_t bytes = off_basis + sizeof(uint64_t) * (size_t)n * h->W;
-    if (cudaMalloc(&h->dmem, bytes) != cudaSuccess) {
+    // Stream-ordered allocation: no device-wide synchronisation, so a serving
+    // loop can create and destroy handles while other work is in flight.
+    hlf::keep_pool_memory();
+    if (cudaMallocAsync(&h->dmem, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return HLF_ERR_NOMEM;
@@ -300,9 +318,17 @@ hlf_status hlf_destroy(hlf_handle* h)
     if (!h) return HLF_OK;
     hlf_status st = HLF_OK;
     {
+        // Freed in stream order after the handle's last work: the host does
+        // not wait, and no device-wide synchronisation happens.
         DeviceGuard g(h->device);
-        if (h->last && cudaEventSynchronize(h->last) != cudaSuccess) st = HLF_ERR_CUDA;
-        if (h->dmem && cudaFree(h->dmem) != cudaSuccess) st = HLF_ERR_CUDA;
+        if (h->dmem) {
+            bool freed = h->priv && h->last && cudaStreamWaitEvent(h->priv, h->last, 0) == cudaSuccess &&
+                         cudaFreeAsync(h->dmem, h->priv) == cudaSuccess;
+            if (!freed) {  // error paths only: a plain synchronising free
+                cudaGetLastError();
+                if (cudaFree(h->dmem) != cudaSuccess) st = HLF_ERR_CUDA;
+            }
+        }
         if (h->last) cudaEventDestroy(h->last);
         if (h->priv) cudaStreamDestroy(h->priv);
     }

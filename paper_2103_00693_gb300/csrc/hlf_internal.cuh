@@ -41,6 +41,10 @@ hlf_status launch_sample(const uint64_t* table, int W, int nb, const uint64_t* i
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Lets the current device's default memory pool keep up to 1 GiB of freed
+// handle memory (called before the first stream-ordered allocation).
+void keep_pool_memory();
+
 // ----------------------------------------------------------- device helpers
 
 // SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014): the

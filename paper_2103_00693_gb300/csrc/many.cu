@@ -235,7 +235,9 @@ hlf_status hlf_enumerate_store_many(hlf_many* m, hlf_handle* const* hs, const ui
     if (cudaMemcpyAsync(m->dev[b], d, sizeof(hlf::WinDesc) * (size_t)used, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return HLF_ERR_CUDA;
-    const uint64_t warps_cap = (uint64_t)hlf::sm_count() * 8 * (hlf::kThreads / 32);
+    // Two CTAs per SM keep HBM busy for stores and leave room on every SM for
+    // the factorisations a serving loop runs alongside.
+    const uint64_t warps_cap = (uint64_t)hlf::sm_count() * 2 * (hlf::kThreads / 32);
     const uint64_t warps = tasks < warps_cap ? tasks : warps_cap;
     const unsigned blocks = (unsigned)((warps * 32 + hlf::kThreads - 1) / hlf::kThreads);
     hlf::many_kernel<<<blocks, hlf::kThreads, 0, s>>>(m->dev[b], used, tasks);

@@ -9,21 +9,29 @@ Once its factorisation is known (rank r), the window is
 and the solutions z(offset) .. z(offset + count - 1) are returned to the host.
 
 Continuous batching (Server.run):
-  * admission: a request is admitted, in arrival order, once it has arrived
-    and the device memory it will hold (its factorisation and its output
-    window) fits in the budget; otherwise it waits;
-  * factorisations are launched on a factor stream and stay resident until
-    their window has been copied out;
+  * admission by device memory: a request is admitted, in arrival order, once
+    it has arrived and its output window (want x W words) fits in the device
+    staging ring; a window that does not fit waits for earlier ones to leave;
+  * factorisations are launched on high-priority factor streams as requests
+    are admitted
+    and stay resident (one handle each) until their window has reached the
+    host;
   * every tick, all admitted windows whose factorisation has finished are
     materialised by ONE hlf_enumerate_store_many launch on the enumeration
-    stream, while earlier ticks' results are still being copied out;
-  * copies go to pinned host buffers on a copy stream; a request completes
-    when its copy event has fired (latency = completion - arrival).
-All solver work runs in the library's kernels; this module only schedules.
+    stream, into the staging ring, while earlier ticks' windows are still
+    being copied out and later requests are being factored;
+  * each window is copied to its slot of a pinned host ring on a copy stream;
+    a request completes when its copy event has fired
+    (latency = completion - arrival).
+Both rings are allocated once, up front, so the loop itself never allocates
+or frees memory (allocation can synchronise the device); handles use the
+stream-ordered pool. All solver work runs in the library's kernels; this
+module only schedules.
 """
 
 from __future__ import annotations
 
+import collections
 import time
 from dataclasses import dataclass, field
 
@@ -44,6 +52,62 @@ def handle_bytes(n: int) -> int:
     return 64 + 4 * n + 8 * 66 * W + 8 * n * W + 1024
 
 
+class Ring:
+    """FIFO arena over one preallocated 1-D int64 tensor. Blocks are carved
+    at the head and reclaimed from the tail in allocation order (a block
+    freed early stays reserved until the blocks before it are freed)."""
+
+    ALIGN = 32  # words (256 bytes)
+
+    def __init__(self, buf):
+        self.buf = buf
+        self.size = buf.numel()
+        self.head = 0
+        self.tail = 0
+        self.live = collections.deque()  # [start, nwords, freed]
+
+    @property
+    def used(self) -> int:
+        if not self.live:
+            return 0
+        return (self.head - self.tail) % self.size or self.size
+
+    def alloc(self, nwords: int):
+        n = max(self.ALIGN, (nwords + self.ALIGN - 1) // self.ALIGN * self.ALIGN)
+        if n > self.size:
+            return None
+        if not self.live:
+            self.head = self.tail = 0
+        if self.live and self.head <= self.tail:        # wrapped: free space is [head, tail)
+            if self.tail - self.head < n:
+                return None
+            start = self.head
+        elif self.size - self.head >= n:                # free: [head, size) and [0, tail)
+            start = self.head
+        elif self.tail >= n and self.live:
+            start = 0
+        else:
+            return None
+        self.head = start + n
+        if self.head == self.size:
+            self.head = 0
+        blk = [start, n, False]
+        self.live.append(blk)
+        return blk
+
+    def view(self, blk, nwords: int):
+        return self.buf[blk[0]: blk[0] + nwords]
+
+    def free(self, blk):
+        blk[2] = True
+        while self.live and self.live[0][2]:
+            self.live.popleft()
+        if self.live:
+            self.tail = self.live[0][0]
+        else:
+            self.head = self.tail = 0
+
+
 @dataclass
 class Req:
     id: int
@@ -58,14 +122,13 @@ class Req:
     count: int = 0
     t_done: float = 0.0
     result: np.ndarray | None = None
-    # device-side state
     h: int = 0
+    blk_dev: list | None = None
+    blk_host: list | None = None
+    blk_in: list | None = None
     A_dev: object = None
-    out_dev: object = None
     ev_factor: object = None
     ev_copy: object = None
-    host: object = None
-    reserved: int = 0
 
 
 @dataclass
@@ -95,18 +158,28 @@ def _mk_reqs(stream: list[dict]) -> list[Req]:
 
 
 class Server:
-    """Continuous-batching server on the current CUDA device."""
+    """Continuous-batching server on the current CUDA device.
 
-    def __init__(self, mem_budget_bytes: int = 16 << 30, max_batch: int = 4096, keep_results: bool = True):
+    device_bytes: the staging ring (the admission budget for output windows);
+    host_bytes:   the pinned host ring the results land in.
+    """
+
+    def __init__(self, device_bytes: int = 8 << 30, host_bytes: int = 8 << 30, max_batch: int = 4096,
+                 keep_results: bool = True):
         import torch
 
-        self.budget = mem_budget_bytes
         self.keep = keep_results
-        self.s_factor = torch.cuda.Stream()
+        # factorisations: several high-priority streams, so single-CTA factor
+        # kernels run side by side and get SMs ahead of the bulk stores
+        self.s_factors = [torch.cuda.Stream(priority=-1) for _ in range(4)]
+        self._next_factor = 0
         self.s_enum = torch.cuda.Stream()
         self.s_copy = torch.cuda.Stream()
         self.max_batch = max_batch
         self.many = hlf.hlf_many_create(max_batch)
+        self.dev_ring = Ring(torch.empty(device_bytes // 8, dtype=torch.int64, device="cuda"))
+        self.host_ring = Ring(torch.empty(host_bytes // 8, dtype=torch.int64, pin_memory=True))
+        self.in_ring = Ring(torch.empty((64 << 20) // 8, dtype=torch.int64, pin_memory=True))
 
     def close(self):
         if self.many:
@@ -119,52 +192,68 @@ class Server:
         except Exception:
             pass
 
+    def _admit(self, q: Req) -> bool:
+        import torch
+
+        q.n = q.A.shape[0]
+        q.W = hlf.words(q.n)
+        words = q.want * q.W
+        bd = self.dev_ring.alloc(words)
+        if bd is None:
+            return False
+        bh = self.host_ring.alloc(words)
+        if bh is None:
+            self.dev_ring.free(bd)
+            return False
+        bi = self.in_ring.alloc(q.n * q.W)
+        if bi is None:
+            self.dev_ring.free(bd)
+            self.host_ring.free(bh)
+            return False
+        q.blk_dev, q.blk_host, q.blk_in = bd, bh, bi
+        staged = self.in_ring.view(bi, q.n * q.W)
+        staged.copy_(torch.from_numpy(hlf.pack_rows(q.A).view(np.int64).ravel()))
+        sf = self.s_factors[self._next_factor]
+        self._next_factor = (self._next_factor + 1) % len(self.s_factors)
+        with torch.cuda.stream(sf):
+            q.A_dev = torch.empty((q.n, q.W), dtype=torch.int64, device="cuda")
+            q.A_dev.view(-1).copy_(staged, non_blocking=True)
+            q.h = hlf.hlf_factor(q.A_dev, q.n, sf)
+            q.ev_factor = torch.cuda.Event()
+            q.ev_factor.record(sf)
+        return True
+
     def run(self, stream: list[dict]) -> tuple[Stats, list[Req]]:
         import torch
 
         reqs = _mk_reqs(stream)
-        waiting = list(reqs)           # not yet admitted, in arrival order
-        factoring: list[Req] = []      # factor launched
-        copying: list[Req] = []        # window launched and copy enqueued
+        waiting = collections.deque(reqs)
+        factoring: list[Req] = []
+        copying: list[Req] = []
         done: list[Req] = []
-        used = 0
         st = Stats(n_requests=len(reqs))
         t0 = time.perf_counter()
         busy_since = None
         while waiting or factoring or copying:
             now = time.perf_counter() - t0
-            # -- admission, in arrival order, by device memory
             while waiting and waiting[0].t_arrival <= now:
-                q = waiting[0]
-                q.n = q.A.shape[0]
-                q.W = hlf.words(q.n)
-                need = handle_bytes(q.n) + q.want * q.W * 8
-                if used + need > self.budget and (factoring or copying):
+                if not self._admit(waiting[0]):
+                    if not (factoring or copying):
+                        raise RuntimeError(f"request {waiting[0].id} does not fit the rings")
                     break
-                waiting.pop(0)
-                q.reserved = need
-                used += need
-                packed = torch.from_numpy(hlf.pack_rows(q.A).view(np.int64)).pin_memory()
-                with torch.cuda.stream(self.s_factor):
-                    q.A_dev = packed.to("cuda", non_blocking=True)
-                    q.h = hlf.hlf_factor(q.A_dev, q.n, self.s_factor)
-                    q.ev_factor = torch.cuda.Event()
-                    q.ev_factor.record(self.s_factor)
-                factoring.append(q)
-            # -- one launch for every window whose factorisation is done
-            ready = [q for q in factoring if q.ev_factor.query()][: self.max_batch]
-            if ready:
+                factoring.append(waiting.popleft())
                 if busy_since is None:
                     busy_since = now
+            ready = [q for q in factoring if q.ev_factor.query()][: self.max_batch]
+            if ready:
                 for q in ready:
                     factoring.remove(q)
+                    self.in_ring.free(q.blk_in)
                     q.r = hlf.hlf_get_rank(q.h)
                     q.offset, q.count = window_of(q.r, q.want, q.u)
-                    used += q.count * q.W * 8 - q.want * q.W * 8  # shrink to the real window
-                    q.reserved += q.count * q.W * 8 - q.want * q.W * 8
-                    q.out_dev = torch.empty((max(q.count, 1), q.W), dtype=torch.int64, device="cuda")
-                hlf.hlf_enumerate_store_many(self.many, [q.h for q in ready], [q.offset for q in ready],
-                                             [q.count for q in ready], [q.out_dev for q in ready], self.s_enum)
+                hlf.hlf_enumerate_store_many(
+                    self.many, [q.h for q in ready], [q.offset for q in ready], [q.count for q in ready],
+                    [self.dev_ring.view(q.blk_dev, max(q.count, 1) * q.W) for q in ready], self.s_enum)
                 st.ticks += 1
                 st.launches += 1
                 ev = torch.cuda.Event()
@@ -172,52 +261,58 @@ class Server:
                 self.s_copy.wait_event(ev)
                 with torch.cuda.stream(self.s_copy):
                     for q in ready:
-                        q.host = torch.empty((max(q.count, 1), q.W), dtype=torch.int64, pin_memory=True)
-                        q.host.copy_(q.out_dev, non_blocking=True)
+                        words = q.count * q.W
+                        self.host_ring.view(q.blk_host, words).copy_(self.dev_ring.view(q.blk_dev, words),
+                                                                     non_blocking=True)
                         q.ev_copy = torch.cuda.Event()
                         q.ev_copy.record(self.s_copy)
                 copying.extend(ready)
-            # -- completions
-            still = []
-            for q in copying:
-                if q.ev_copy.query():
-                    q.t_done = time.perf_counter() - t0
-                    st.latencies_ms.append(1e3 * (q.t_done - q.t_arrival))
-                    st.solutions += q.count
-                    st.bytes_out += q.count * q.W * 8
-                    if self.keep:
-                        q.result = q.host.numpy()[: q.count].view(np.uint64).copy()
-                    hlf.hlf_destroy(q.h)
-                    q.h = 0
-                    q.out_dev = q.A_dev = q.host = None
-                    used -= q.reserved
-                    done.append(q)
-                else:
-                    still.append(q)
-            copying = still
+            finished = 0
+            while copying and copying[0].ev_copy.query():  # copies complete in stream order
+                q = copying.pop(0)
+                finished += 1
+                q.t_done = time.perf_counter() - t0
+                st.latencies_ms.append(1e3 * (q.t_done - q.t_arrival))
+                st.solutions += q.count
+                st.bytes_out += q.count * q.W * 8
+                if self.keep:
+                    q.result = self.host_ring.view(q.blk_host, q.count * q.W).numpy().view(np.uint64)\
+                        .reshape(q.count, q.W).copy()
+                hlf.hlf_destroy(q.h)
+                q.h = 0
+                q.A_dev = None
+                self.dev_ring.free(q.blk_dev)
+                self.host_ring.free(q.blk_host)
+                done.append(q)
             if busy_since is not None and not (factoring or copying):
                 st.busy_s += (time.perf_counter() - t0) - busy_since
                 busy_since = None
-            if not ready and not (copying and copying[0].ev_copy.query()):
+            if not ready and not finished:
                 if waiting and not factoring and not copying:
                     dt = waiting[0].t_arrival - (time.perf_counter() - t0)
                     if dt > 0:
-                        time.sleep(min(dt, 0.002))
+                        time.sleep(min(dt, 0.001))
                 else:
-                    time.sleep(20e-6)
+                    time.sleep(10e-6)
         st.makespan_s = time.perf_counter() - t0
         if busy_since is not None:
             st.busy_s += st.makespan_s - busy_since
         return st, done
 
 
-def run_plain(stream: list[dict], keep_results: bool = True) -> tuple[Stats, list[Req]]:
+def run_plain(stream: list[dict], keep_results: bool = True, host_bytes: int = 2 << 30,
+              device_bytes: int = 2 << 30) -> tuple[Stats, list[Req]]:
     """The plain path: requests served one at a time in arrival order, each
-    with its own factor launch, window launch and copy, synchronously."""
+    with its own factor launch, window launch and copy to pinned host memory,
+    waiting for each step. It uses the same preallocated buffers, so it
+    differs from Server.run only in scheduling."""
     import torch
 
     reqs = _mk_reqs(stream)
     st = Stats(n_requests=len(reqs))
+    dev_buf = torch.empty(device_bytes // 8, dtype=torch.int64, device="cuda")
+    host_buf = torch.empty(host_bytes // 8, dtype=torch.int64, pin_memory=True)
+    in_buf = torch.empty((1 << 20) // 8, dtype=torch.int64, pin_memory=True)
     t0 = time.perf_counter()
     for q in reqs:
         now = time.perf_counter() - t0
@@ -226,23 +321,23 @@ def run_plain(stream: list[dict], keep_results: bool = True) -> tuple[Stats, lis
         t_start = time.perf_counter() - t0
         q.n = q.A.shape[0]
         q.W = hlf.words(q.n)
-        A_dev = torch.from_numpy(hlf.pack_rows(q.A).view(np.int64)).cuda()
+        in_buf[: q.n * q.W].copy_(torch.from_numpy(hlf.pack_rows(q.A).view(np.int64).ravel()))
+        A_dev = in_buf[: q.n * q.W].view(q.n, q.W).to("cuda", non_blocking=True)
         h = hlf.hlf_factor(A_dev, q.n)
         q.r = hlf.hlf_get_rank(h)
         q.offset, q.count = window_of(q.r, q.want, q.u)
-        out = torch.empty((max(q.count, 1), q.W), dtype=torch.int64, device="cuda")
-        hlf.hlf_enumerate_store(h, q.offset, q.count, out)
-        host = torch.empty((max(q.count, 1), q.W), dtype=torch.int64, pin_memory=True)
-        host.copy_(out)
+        words = q.count * q.W
+        hlf.hlf_enumerate_store(h, q.offset, q.count, dev_buf[: max(words, 1)])
+        host_buf[:words].copy_(dev_buf[:words])
         hlf.hlf_destroy(h)
         q.t_done = time.perf_counter() - t0
         st.busy_s += q.t_done - t_start
         st.launches += 2
         st.latencies_ms.append(1e3 * (q.t_done - q.t_arrival))
         st.solutions += q.count
-        st.bytes_out += q.count * q.W * 8
+        st.bytes_out += words * 8
         if keep_results:
-            q.result = host.numpy()[: q.count].view(np.uint64).copy()
+            q.result = host_buf[:words].numpy().view(np.uint64).reshape(q.count, q.W).copy()
     st.makespan_s = time.perf_counter() - t0
     st.ticks = len(reqs)
     return st, reqs

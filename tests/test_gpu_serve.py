@@ -18,7 +18,7 @@ def _stream(count, rate, seed, N_hi=12, lo=4, hi=12):
 
 def test_served_equals_alone_and_oracle(cuda_ok):
     reqs = _stream(80, 5000.0, 7)
-    srv = serve.Server(mem_budget_bytes=64 << 20)
+    srv = serve.Server(device_bytes=64 << 20, host_bytes=64 << 20)
     st, done = srv.run(reqs)
     srv.close()
     assert st.n_requests == len(done) == len(reqs)
@@ -39,7 +39,7 @@ def test_served_under_tight_memory_budget(cuda_ok):
     """A budget that fits only a few windows at once still serves everything
     exactly (requests wait for admission)."""
     reqs = _stream(40, 20000.0, 9, N_hi=20, lo=8, hi=14)
-    srv = serve.Server(mem_budget_bytes=1 << 20)
+    srv = serve.Server(device_bytes=1 << 20, host_bytes=4 << 20)
     st, done = srv.run(reqs)
     srv.close()
     assert len(done) == len(reqs)
@@ -54,7 +54,7 @@ def test_served_large_windows_mixed_sizes(cuda_ok):
     from synth import workloads as wl
 
     reqs = wl.stream(12, 200.0)
-    srv = serve.Server()
+    srv = serve.Server(device_bytes=4 << 30, host_bytes=4 << 30)
     st, done = srv.run(reqs)
     srv.close()
     _, alone = serve.run_plain(reqs)

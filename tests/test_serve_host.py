@@ -41,3 +41,44 @@ def test_stream_workload_shape():
     assert len(reqs) == 50
     assert all(9 <= q["A"].shape[0] <= 1024 for q in reqs)
     assert all((1 << 10) <= q["want"] <= (1 << 24) for q in reqs)
+
+
+def test_ring_blocks_never_overlap():
+    """Random allocate/free sequences on the FIFO arena: live blocks stay in
+    bounds and disjoint, and everything is reclaimed at the end."""
+    import torch
+
+    rng = np.random.default_rng(3)
+    ring = serve.Ring(torch.empty(10_240, dtype=torch.int64))
+    live = []
+    for step in range(20000):
+        if live and (rng.random() < 0.45 or len(live) > 40):
+            blk = live.pop(int(rng.integers(0, len(live))))
+            ring.free(blk)
+        else:
+            n = int(rng.integers(1, 3000))
+            blk = ring.alloc(n)
+            if blk is not None:
+                assert blk[1] >= n
+                live.append(blk)
+        spans = sorted((b[0], b[0] + b[1]) for b in live)
+        for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+            assert a1 <= b0
+        assert all(0 <= a and b <= ring.size for a, b in spans)
+    for blk in live:
+        ring.free(blk)
+    assert ring.used == 0 and ring.alloc(ring.size) is not None
+
+
+def test_ring_fifo_reuse_and_refusal():
+    import torch
+
+    ring = serve.Ring(torch.empty(1024, dtype=torch.int64))
+    a = ring.alloc(500)
+    b = ring.alloc(500)
+    assert a[0] == 0 and b[0] == 512
+    assert ring.alloc(100) is None  # full
+    ring.free(b)                    # freed out of order: still held by a
+    assert ring.alloc(100) is None
+    ring.free(a)
+    assert ring.alloc(1024)[0] == 0

@@ -116,6 +116,22 @@ hlf_status hlf_get_rank(hlf_handle* h, int32_t* r);
  * z0_host[W], basis_host[r][W] (B_k, row-major). */
 hlf_status hlf_get_factor(hlf_handle* h, int32_t* piv_host, uint64_t* z0_host, uint64_t* basis_host);
 
+/* Enumeration orders. HLF_ORDER_GRAY (the default) is the order of the
+ * conventions above. HLF_ORDER_PAPER is the paper's own order (Section 2,
+ * Eq. 3, with the binary counter of Section 4): index t sets
+ * R_{p_j} = bit (r - j) of t (R^(r) = R_{p_1}..R_{p_r} read as a binary
+ * numeral, R_{p_1} most significant; bits of t at or above 64 are 0), every
+ * other R_i = 0, and the solution is y ^ z^a with y = A R over GF(2). Both
+ * orders enumerate the same set: every index in [0, 2^min(r,64)) names one
+ * solution, different indices name different solutions. */
+#define HLF_ORDER_GRAY 0
+#define HLF_ORDER_PAPER 1
+
+/* Selects the order used by every later hlf_enumerate_*, hlf_sample and
+ * hlf_enumerate_store_many call on h. Host-side only; takes effect for work
+ * enqueued after it. */
+hlf_status hlf_set_order(hlf_handle* h, int32_t order);
+
 /* n and W of the handle's matrix. */
 hlf_status hlf_get_shape(hlf_handle* h, int32_t* n, int32_t* W);
 

@@ -346,12 +346,13 @@ int orc_reduce(const uint8_t* R, const uint8_t* z0, int n, int r, uint64_t offse
 
 /* The paper's order (Section 2, Eq. 3; the counter of Section 4): counter
  * value t in [t0, t0+count) sets R_{p_j} to bit (r - j) of t (R^(r) read as
- * a binary numeral, R_{p_1} most significant), every other R_i to 0;
- * y_i = XOR_j A_ij R_j; z = y XOR z^a. Output out[count][W], packed. */
+ * a binary numeral, R_{p_1} most significant; a 64-bit counter has no bits at
+ * or above 64, so for r > 64 the leading R_{p_j} stay 0), every other R_i to
+ * 0; y_i = XOR_j A_ij R_j; z = y XOR z^a. Output out[count][W], packed. */
 int orc_paper_order(const uint8_t* A, const int32_t* piv, int r, const uint8_t* z0, int n,
                     uint64_t t0, uint64_t count, uint64_t* out)
 {
-    if (!A || !piv || !z0 || (!out && count) || n < 1 || r < 0 || r > n || r > 63) return ORC_ERR_ARG;
+    if (!A || !piv || !z0 || (!out && count) || n < 1 || r < 0 || r > n) return ORC_ERR_ARG;
     if (!window_ok(r, t0, count)) return ORC_ERR_RANGE;
     int W = words_of(n);
     uint8_t* R = (uint8_t*)malloc((size_t)n);
@@ -360,7 +361,7 @@ int orc_paper_order(const uint8_t* A, const int32_t* piv, int r, const uint8_t* 
     for (uint64_t c = 0; c < count; ++c) {
         uint64_t t = t0 + c;
         memset(R, 0, (size_t)n);
-        for (int j = 1; j <= r; ++j) R[piv[j - 1]] = (uint8_t)((t >> (r - j)) & 1);
+        for (int j = 1; j <= r; ++j) R[piv[j - 1]] = r - j < 64 ? (uint8_t)((t >> (r - j)) & 1) : 0;
         for (int i = 0; i < n; ++i) {
             uint8_t y = 0;
             for (int j = 0; j < n; ++j) y ^= (uint8_t)(A[(size_t)i * n + j] & R[j]);

@@ -74,7 +74,7 @@ constexpr size_t batch_smem_bytes()
 template <int W>
 __device__ void batch_factor(const BatchArgs& a, int b, int n, unsigned char* smem)
 {
-    FactorOut o{nullptr, nullptr, a.tables + (size_t)b * kTableSlot, a.info + 2 * b};
+    FactorOut o{nullptr, nullptr, a.tables + (size_t)b * kTableSlot, a.info + 2 * b, nullptr};
     factor_block<W, 1, kBatchMaxN>(a.A + a.word_off[b], n, o, smem);
 }
 

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const uint64_t* __rest
         const uint64_t i = idx[j];
         uint64_t z[W];
         if (nb < 64 && (i >> nb)) {
-            set_status(info, HLF_ERR_RANGE);
+            *reinterpret_cast<volatile int32_t*>(info) = HLF_ERR_RANGE;  // host-mapped status word
 #pragma unroll
             for (int w = 0; w < W; ++w) z[w] = 0;
         } else {

@@ -214,6 +214,24 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
     __syncthreads();
     const int e = sm.err;
     if (tid < W) o.table[kTableZ0Row * W + tid] = sm.z0[tid];
+
+    // ---- the paper's own order (Section 2, Eq. 3; the counter of Section 4):
+    // counter value t sets R_{p_j} = bit (r - j) of t, y = A R, z = y ^ z^a.
+    // Bit l of t selects T_l = column p_{r-1-l} of A (0-based pivots), which is
+    // row p_{r-1-l} since A is symmetric. With P_k = T_0 ^ ... ^ T_k, the Gray
+    // walk over P visits z(t) in counter order, because bit l of t is the XOR
+    // of the Gray code's bits k >= l. One warp builds the prefix XORs.
+    if (o.ptable) {
+        if (warp == 0 && lane < W) {
+            uint64_t acc = 0;
+            for (int l = 0; l < nb; ++l) {
+                acc ^= A[(size_t)sm.pivcol[r - 1 - l] * W + lane];
+                o.ptable[l * W + lane] = acc;
+            }
+        }
+        for (int i = nb * W + tid; i < kTableRows * W; i += bs) o.ptable[i] = 0ull;
+        if (tid < W) o.ptable[kTableZ0Row * W + tid] = sm.z0[tid];
+    }
     if (tid == 0) {
         o.info[0] = e;
         o.info[1] = e ? -1 : r;

@@ -2,7 +2,9 @@
 // and its device buffers, and the launches of the stage-1 and stage-2 kernels.
 
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "hlf_internal.cuh"
 
@@ -11,12 +13,21 @@ struct hlf_handle {
     int32_t W = 0;
     int device = 0;
     unsigned char* dmem = nullptr;  // one allocation: info | piv | table | basis
-    int32_t* info = nullptr;
+    int32_t* info = nullptr;         // status word: pinned host memory, device-mapped
+    int32_t* info_dev = nullptr;     // the same words as the kernels address them
     int32_t* piv = nullptr;
     uint64_t* table = nullptr;
+    uint64_t* ptable = nullptr;     // the paper-order table
     uint64_t* basis = nullptr;
-    cudaEvent_t last = nullptr;     // recorded after the last work enqueued through the handle
-    cudaStream_t priv = nullptr;    // private non-blocking stream for status reads
+    int32_t order = HLF_ORDER_GRAY; // which table the stage-2 calls read
+    cudaEvent_t factored = nullptr;  // recorded after the factor kernel
+    // one event per stream the handle has been used on, recorded after the
+    // latest work on that stream (hlf_destroy and hlf_get_status wait for all)
+    static constexpr int kMaxStreams = 8;
+    cudaStream_t use_stream[kMaxStreams] = {};
+    cudaEvent_t use_event[kMaxStreams] = {};
+    int n_uses = 0;
+    cudaStream_t priv = nullptr;     // private non-blocking stream for status reads
     bool rank_known = false;
     int32_t r = -1;
 };
@@ -44,12 +55,58 @@ struct DeviceGuard {
     }
 };
 
-hlf_status read_info(hlf_handle* h, int32_t out[2])
+// Status words live in pinned, device-mapped host memory: kernels store them
+// directly and the host reads them after an event, with no copy. A copy
+// would queue behind whatever large transfers the copy engines are busy
+// with, which stalls a serving loop. Slabs are allocated on first need and
+// kept until the process exits; slots are recycled.
+constexpr int kSlotWords = 16;
+constexpr int kSlotsPerSlab = 4096;
+std::mutex g_slot_mu;
+std::vector<int32_t*> g_free_slots;
+
+int32_t* acquire_status_slot()
 {
-    if (cudaEventSynchronize(h->last) != cudaSuccess) return HLF_ERR_CUDA;
-    if (cudaMemcpyAsync(out, h->info, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->priv) != cudaSuccess)
-        return HLF_ERR_CUDA;
-    if (cudaStreamSynchronize(h->priv) != cudaSuccess) return HLF_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    if (g_free_slots.empty()) {
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(int32_t) * kSlotWords * kSlotsPerSlab,
+                          cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        int32_t* base = static_cast<int32_t*>(p);
+        for (int i = kSlotsPerSlab - 1; i >= 0; --i) g_free_slots.push_back(base + i * kSlotWords);
+    }
+    int32_t* slot = g_free_slots.back();
+    g_free_slots.pop_back();
+    std::memset(slot, 0, sizeof(int32_t) * kSlotWords);
+    return slot;
+}
+
+void release_status_slot(int32_t* slot)
+{
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    g_free_slots.push_back(slot);
+}
+
+// Host callback (no CUDA calls allowed in it): recycle a status slot.
+void CUDART_CB release_slot_cb(void* slot) { release_status_slot(static_cast<int32_t*>(slot)); }
+
+// Host wait for every stream's latest work through h.
+hlf_status wait_uses(hlf_handle* h)
+{
+    for (int i = 0; i < h->n_uses; ++i)
+        if (cudaEventSynchronize(h->use_event[i]) != cudaSuccess) return HLF_ERR_CUDA;
+    return HLF_OK;
+}
+
+hlf_status read_info(hlf_handle* h, int32_t out[2], bool all_uses)
+{
+    if (all_uses ? wait_uses(h) != HLF_OK : cudaEventSynchronize(h->factored) != cudaSuccess) return HLF_ERR_CUDA;
+    const volatile int32_t* w = h->info;
+    out[0] = w[0];
+    out[1] = w[1];
     return HLF_OK;
 }
 
@@ -57,13 +114,15 @@ hlf_status ensure_rank(hlf_handle* h)
 {
     if (h->rank_known) return HLF_OK;
     int32_t info[2];
-    hlf_status st = read_info(h, info);
+    hlf_status st = read_info(h, info, false);
     if (st != HLF_OK) return st;
     if (info[0] != HLF_OK) return (hlf_status)info[0];
     h->r = info[1];
     h->rank_known = true;
     return HLF_OK;
 }
+
+const uint64_t* enum_table(const hlf_handle* h) { return h->order == HLF_ORDER_PAPER ? h->ptable : h->table; }
 
 // Is [offset, offset + count) inside [0, 2^min(r, 64))?
 bool window_ok(int32_t r, uint64_t offset, uint64_t count)
@@ -75,10 +134,36 @@ bool window_ok(int32_t r, uint64_t offset, uint64_t count)
     return count == 0 || count - 1 <= ~0ull - offset;
 }
 
+}  // namespace
+
+namespace hlf {
+
+// Record that work reading or writing h's buffers was enqueued on s.
+hlf_status handle_record_use(hlf_handle* h, cudaStream_t s)
+{
+    for (int i = 0; i < h->n_uses; ++i)
+        if (h->use_stream[i] == s) return cudaEventRecord(h->use_event[i], s) == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+    int slot = h->n_uses;
+    if (slot == hlf_handle::kMaxStreams) {  // table full: retire the oldest stream's event
+        if (cudaEventSynchronize(h->use_event[0]) != cudaSuccess) return HLF_ERR_CUDA;
+        slot = 0;
+    } else {
+        if (cudaEventCreateWithFlags(&h->use_event[slot], cudaEventDisableTiming) != cudaSuccess)
+            return HLF_ERR_CUDA;
+        ++h->n_uses;
+    }
+    h->use_stream[slot] = s;
+    return cudaEventRecord(h->use_event[slot], s) == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+}
+
+}  // namespace hlf
+
+namespace {
+
 hlf_status after_launch(hlf_handle* h, hlf_status st, cudaStream_t s)
 {
     if (st != HLF_OK) return st;
-    return cudaEventRecord(h->last, s) == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+    return hlf::handle_record_use(h, s);
 }
 
 }  // namespace
@@ -92,7 +177,7 @@ hlf_status handle_enum_view(hlf_handle* h, const uint64_t** table, int32_t* r, i
     if (!g.ok) return HLF_ERR_CUDA;
     hlf_status st = ensure_rank(h);
     if (st != HLF_OK) return st;
-    *table = h->table;
+    *table = enum_table(h);
     *r = h->r;
     *W = h->W;
     return HLF_OK;
@@ -170,7 +255,8 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
     }
     const size_t off_piv = 64;
     const size_t off_table = round_up(off_piv + sizeof(int32_t) * n, 256);
-    const size_t off_basis = round_up(off_table + sizeof(uint64_t) * hlf::kTableTotalRows * h->W, 256);
+    const size_t off_ptable = round_up(off_table + sizeof(uint64_t) * hlf::kTableTotalRows * h->W, 256);
+    const size_t off_basis = round_up(off_ptable + sizeof(uint64_t) * hlf::kTableTotalRows * h->W, 256);
     const size_t bytes = off_basis + sizeof(uint64_t) * (size_t)n * h->W;
     // Stream-ordered allocation: no device-wide synchronisation, so a serving
     // loop can create and destroy handles while other work is in flight.
@@ -180,17 +266,24 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
         delete h;
         return HLF_ERR_NOMEM;
     }
-    h->info = reinterpret_cast<int32_t*>(h->dmem);
+    h->info = acquire_status_slot();
+    if (!h->info || cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->info_dev), h->info, 0) != cudaSuccess) {
+        cudaGetLastError();
+        hlf_destroy(h);
+        return HLF_ERR_NOMEM;
+    }
     h->piv = reinterpret_cast<int32_t*>(h->dmem + off_piv);
     h->table = reinterpret_cast<uint64_t*>(h->dmem + off_table);
+    h->ptable = reinterpret_cast<uint64_t*>(h->dmem + off_ptable);
     h->basis = reinterpret_cast<uint64_t*>(h->dmem + off_basis);
-    if (cudaEventCreateWithFlags(&h->last, cudaEventDisableTiming) != cudaSuccess ||
+    if (cudaEventCreateWithFlags(&h->factored, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking) != cudaSuccess) {
         hlf_destroy(h);
         return HLF_ERR_CUDA;
     }
-    hlf::FactorOut o{h->basis, h->piv, h->table, h->info};
+    hlf::FactorOut o{h->basis, h->piv, h->table, h->info_dev, h->ptable};
     hlf_status st = hlf::launch_factor(A_dev, n, h->W, o, s);
+    if (st == HLF_OK && cudaEventRecord(h->factored, s) != cudaSuccess) st = HLF_ERR_CUDA;
     st = after_launch(h, st, s);
     if (st != HLF_OK) {
         hlf_destroy(h);
@@ -208,6 +301,13 @@ hlf_status hlf_get_rank(hlf_handle* h, int32_t* r)
     hlf_status st = ensure_rank(h);
     if (st != HLF_OK) return st;
     *r = h->r;
+    return HLF_OK;
+}
+
+hlf_status hlf_set_order(hlf_handle* h, int32_t order)
+{
+    if (!h || (order != HLF_ORDER_GRAY && order != HLF_ORDER_PAPER)) return HLF_ERR_ARG;
+    h->order = order;
     return HLF_OK;
 }
 
@@ -246,14 +346,9 @@ hlf_status hlf_get_status(hlf_handle* h)
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
     int32_t info[2];
-    hlf_status st = read_info(h, info);
+    hlf_status st = read_info(h, info, true);
     if (st != HLF_OK) return st;
-    if (info[0] != HLF_OK) {
-        const int32_t zero = 0;
-        if (cudaMemcpyAsync(h->info, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->priv) != cudaSuccess ||
-            cudaStreamSynchronize(h->priv) != cudaSuccess)
-            return HLF_ERR_CUDA;
-    }
+    if (info[0] != HLF_OK) *const_cast<volatile int32_t*>(h->info) = 0;  // all work through h is done
     return (hlf_status)info[0];
 }
 
@@ -268,7 +363,7 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
     if (!window_ok(h->r, offset, count)) return HLF_ERR_RANGE;
     if (count == 0) return HLF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return after_launch(h, hlf::launch_store(h->table, h->W, offset, count, out_dev, s), s);
+    return after_launch(h, hlf::launch_store(enum_table(h), h->W, offset, count, out_dev, s), s);
 }
 
 hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, hlf_reduce* red_dev, void* stream)
@@ -282,7 +377,7 @@ hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(red_dev, 0, sizeof(hlf_reduce), s) != cudaSuccess) return HLF_ERR_CUDA;
     if (count == 0) return after_launch(h, HLF_OK, s);
-    return after_launch(h, hlf::launch_reduce(h->table, h->W, offset, count, red_dev, s), s);
+    return after_launch(h, hlf::launch_reduce(enum_table(h), h->W, offset, count, red_dev, s), s);
 }
 
 hlf_status hlf_enumerate_reduce_chunks(hlf_handle* h, uint64_t offset, uint64_t chunk, uint64_t n_chunks,
@@ -297,7 +392,7 @@ hlf_status hlf_enumerate_reduce_chunks(hlf_handle* h, uint64_t offset, uint64_t 
     if (!window_ok(h->r, offset, chunk * n_chunks)) return HLF_ERR_RANGE;
     if (n_chunks == 0) return HLF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return after_launch(h, hlf::launch_reduce_chunks(h->table, h->W, offset, chunk, n_chunks, red_dev, s), s);
+    return after_launch(h, hlf::launch_reduce_chunks(enum_table(h), h->W, offset, chunk, n_chunks, red_dev, s), s);
 }
 
 hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64_t* out_dev, void* stream)
@@ -310,7 +405,7 @@ hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64
     if (m == 0) return HLF_OK;
     const int nb = h->r < HLF_MAX_VARYING ? h->r : HLF_MAX_VARYING;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return after_launch(h, hlf::launch_sample(h->table, h->W, nb, idx_dev, m, out_dev, h->info, s), s);
+    return after_launch(h, hlf::launch_sample(enum_table(h), h->W, nb, idx_dev, m, out_dev, h->info_dev, s), s);
 }
 
 hlf_status hlf_destroy(hlf_handle* h)
@@ -318,18 +413,23 @@ hlf_status hlf_destroy(hlf_handle* h)
     if (!h) return HLF_OK;
     hlf_status st = HLF_OK;
     {
-        // Freed in stream order after the handle's last work: the host does
-        // not wait, and no device-wide synchronisation happens.
+        // Device memory is freed, and the status slot recycled, in stream
+        // order after the latest work on every stream that used the handle:
+        // the host does not wait and no device-wide synchronisation happens.
         DeviceGuard g(h->device);
-        if (h->dmem) {
-            bool freed = h->priv && h->last && cudaStreamWaitEvent(h->priv, h->last, 0) == cudaSuccess &&
-                         cudaFreeAsync(h->dmem, h->priv) == cudaSuccess;
-            if (!freed) {  // error paths only: a plain synchronising free
-                cudaGetLastError();
-                if (cudaFree(h->dmem) != cudaSuccess) st = HLF_ERR_CUDA;
-            }
+        bool queued = h->priv != nullptr;
+        for (int i = 0; queued && i < h->n_uses; ++i)
+            queued = cudaStreamWaitEvent(h->priv, h->use_event[i], 0) == cudaSuccess;
+        if (queued && h->dmem) queued = cudaFreeAsync(h->dmem, h->priv) == cudaSuccess;
+        if (queued && h->info) queued = cudaLaunchHostFunc(h->priv, release_slot_cb, h->info) == cudaSuccess;
+        if (!queued) {  // error paths only: wait, then release synchronously
+            cudaGetLastError();
+            wait_uses(h);
+            if (h->dmem && cudaFree(h->dmem) != cudaSuccess) st = HLF_ERR_CUDA;
+            if (h->info) release_status_slot(h->info);
         }
-        if (h->last) cudaEventDestroy(h->last);
+        for (int i = 0; i < h->n_uses; ++i) cudaEventDestroy(h->use_event[i]);
+        if (h->factored) cudaEventDestroy(h->factored);
         if (h->priv) cudaStreamDestroy(h->priv);
     }
     delete h;

@@ -1,12 +1,18 @@
 // Internal declarations shared by the kernels and the C ABI of libhlf.
 //
 // Device-side layout of one factorisation (all written by the factor kernel):
-//   info  [16] int32   info[0] = status (hlf_status), info[1] = rank r
+//   info  [16] int32   info[0] = status (hlf_status), info[1] = rank r; these
+//                      live in pinned, device-mapped host memory, so the host
+//                      reads them after an event without a copy
 //   piv   [n]  int32   pivot columns p_0 < ... < p_{r-1}
 //   basis [n][W]       B_0 .. B_{r-1}: the nonzero RREF rows in pivot order
 //   table [66][W]      enumeration table: rows 0..64 hold B_0 .. B_63 with the
 //                      rows k >= min(r, 64) zero (row 64 is always zero, it is
 //                      the target of ctz = 64 steps), row 65 holds z0.
+//   ptable [66][W]     the same layout for the paper's own order: row k is
+//                      T_0 ^ ... ^ T_k with T_l = A's column at pivot p_{r-1-l},
+//                      so that the Gray walk over ptable visits the paper's
+//                      binary counter order (see factor_impl.cuh).
 #pragma once
 
 #include <cstdint>
@@ -21,10 +27,11 @@ constexpr int kTableZ0Row = 65;     // z0 follows the basis rows
 constexpr int kTableTotalRows = 66;
 
 struct FactorOut {
-    uint64_t* basis;  // [n][W]
-    int32_t* piv;     // [n]
-    uint64_t* table;  // [66][W]
-    int32_t* info;    // [16]
+    uint64_t* basis;   // [n][W]
+    int32_t* piv;      // [n]
+    uint64_t* table;   // [66][W]
+    int32_t* info;     // [16]
+    uint64_t* ptable;  // [66][W] or null: the paper-order table (see factor_impl.cuh)
 };
 
 // ---------------------------------------------------------------- launchers

@@ -154,8 +154,10 @@ void plan_window(WinDesc& d, uint32_t W)
 
 }  // namespace
 
-// The handle's enumeration table, rank and word count (defined in hlf_api.cu).
+// The handle's enumeration table, rank and word count, and the record of a
+// use of the handle on a stream (defined in hlf_api.cu).
 hlf_status handle_enum_view(hlf_handle* h, const uint64_t** table, int32_t* r, int32_t* W);
+hlf_status handle_record_use(hlf_handle* h, cudaStream_t s);
 
 }  // namespace hlf
 
@@ -243,6 +245,12 @@ hlf_status hlf_enumerate_store_many(hlf_many* m, hlf_handle* const* hs, const ui
     hlf::many_kernel<<<blocks, hlf::kThreads, 0, s>>>(m->dev[b], used, tasks);
     if (cudaGetLastError() != cudaSuccess) return HLF_ERR_CUDA;
     if (cudaEventRecord(m->done[b], s) != cudaSuccess) return HLF_ERR_CUDA;
+    // every handle read by this launch must outlive it (hlf_destroy waits)
+    for (int32_t j = 0; j < k; ++j) {
+        if (j > 0 && hs[j] == hs[j - 1]) continue;
+        hlf_status st = hlf::handle_record_use(hs[j], s);
+        if (st != HLF_OK) return st;
+    }
     m->next = 1 - b;
     return HLF_OK;
 }

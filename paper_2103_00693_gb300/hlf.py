@@ -44,6 +44,7 @@ SIGNATURES = {
     "hlf_get_rank": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "hlf_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "hlf_get_shape": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "hlf_set_order": (ctypes.c_int, [_vp, _i32]),
     "hlf_get_status": (ctypes.c_int, [_vp]),
     "hlf_enumerate_store": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_reduce": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
@@ -172,6 +173,14 @@ def hlf_get_rank(h: int) -> int:
     r = _i32()
     _check(load().hlf_get_rank(h, ctypes.byref(r)), "hlf_get_rank")
     return r.value
+
+
+ORDER_GRAY = 0
+ORDER_PAPER = 1
+
+
+def hlf_set_order(h: int, order: int):
+    _check(load().hlf_set_order(h, order), "hlf_set_order")
 
 
 def hlf_get_shape(h: int) -> tuple[int, int]:
@@ -356,6 +365,10 @@ class Factorization:
 
     def status(self) -> int:
         return hlf_get_status(self.h)
+
+    def set_order(self, order: int):
+        """ORDER_GRAY (default) or ORDER_PAPER for the later stage-2 calls."""
+        hlf_set_order(self.h, order)
 
     def close(self):
         if self.h:

@@ -32,6 +32,8 @@ module only schedules.
 from __future__ import annotations
 
 import collections
+import contextlib
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -153,6 +155,21 @@ class Stats:
                 "ticks": self.ticks, "launches": self.launches}
 
 
+@contextlib.contextmanager
+def _no_gc_pauses():
+    """Python's cyclic collector can pause the loop for tens of milliseconds
+    when many objects are alive; latency-critical loops keep it off and
+    collect afterwards."""
+    was = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+
+
 def _mk_reqs(stream: list[dict]) -> list[Req]:
     return [Req(id=q["id"], t_arrival=q["t_arrival"], A=q["A"], want=q["want"], u=q["u"]) for q in stream]
 
@@ -224,6 +241,10 @@ class Server:
         return True
 
     def run(self, stream: list[dict]) -> tuple[Stats, list[Req]]:
+        with _no_gc_pauses():
+            return self._run(stream)
+
+    def _run(self, stream: list[dict]) -> tuple[Stats, list[Req]]:
         import torch
 
         reqs = _mk_reqs(stream)
@@ -304,8 +325,14 @@ def run_plain(stream: list[dict], keep_results: bool = True, host_bytes: int = 2
               device_bytes: int = 2 << 30) -> tuple[Stats, list[Req]]:
     """The plain path: requests served one at a time in arrival order, each
     with its own factor launch, window launch and copy to pinned host memory,
-    waiting for each step. It uses the same preallocated buffers, so it
-    differs from Server.run only in scheduling."""
+    waiting for each step. It uses the same kind of preallocated buffers and
+    the same collector setting, so it differs from Server.run only in
+    scheduling."""
+    with _no_gc_pauses():
+        return _run_plain(stream, keep_results, host_bytes, device_bytes)
+
+
+def _run_plain(stream, keep_results, host_bytes, device_bytes):
     import torch
 
     reqs = _mk_reqs(stream)

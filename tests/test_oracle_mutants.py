@@ -26,8 +26,8 @@ MUTANTS = {
                          "for (int k = 1; k < r; ++k) M[(size_t)(nf + k) * (n + 1) + piv[k]] = 1;"),
     "gray_step_wrong_index": ("int k = ctz64(i);", "int k = ctz64(i) + (i > 8 ? 1 : 0);"),
     "fold_or_not_xor": ("t->fold[w] ^= z[w];", "t->fold[w] |= z[w];"),
-    "paper_counter_bit": ("R[piv[j - 1]] = (uint8_t)((t >> (r - j)) & 1);",
-                          "R[piv[j - 1]] = (uint8_t)((t >> (j - 1 + (j == r))) & 1);"),
+    "paper_counter_bit": ("R[piv[j - 1]] = r - j < 64 ? (uint8_t)((t >> (r - j)) & 1) : 0;",
+                          "R[piv[j - 1]] = r - j < 64 ? (uint8_t)((t >> (j - 1 + (j == r))) & 1) : 0;"),
     "rref_skips_rows_above": ("if (i == rank || !M[(size_t)i * cols + c]) continue;",
                               "if (i <= rank || !M[(size_t)i * cols + c]) continue;"),
 }

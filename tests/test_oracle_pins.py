@@ -286,3 +286,18 @@ def test_large_n_factor_consistency():
     assert np.all(F.q % 2 == 0)
     assert np.array_equal((X @ F.z0.astype(np.int64)) % 2, F.q // 2)
     assert not F.z0[F.piv].any()
+
+
+def test_paper_order_beyond_64_pivots():
+    """r > 64: the paper order's 64-bit counter reaches the first 2^64 values;
+    each is a valid solution and the counter is recovered from z on the
+    pivots (bit r-j of t is R_{p_j}, and z restricted to P determines R)."""
+    A = synth.grid_instance(20, 0.5, 1234)
+    F = oc.factor(A)
+    assert F.r > 64
+    top = 1 << 64
+    for t0, cnt in ((0, 300), (top - 300, 300), ((1 << 63) - 5, 10)):
+        Z = oc.unpack_rows(oc.paper_order(F, t0, cnt), F.n).astype(np.int64)
+        par = (Z @ F.X.T.astype(np.int64)) % 2
+        assert np.array_equal(par, np.broadcast_to(F.q // 2, par.shape))
+        assert len({tuple(z) for z in Z}) == cnt

@@ -331,6 +331,7 @@ def run_hlf(args, world, rank, local):
             "gpu_launches": 4 * args.steps,
             "clocks": clk}
 
+    line["next_rows"] = run_next_rows(args, A_dev, n, W, store_n, pk, dev)
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, world, dev, A, r, total, store_n, idx_host)
     del out, smp
@@ -343,6 +344,43 @@ def run_hlf(args, world, rank, local):
         line["cpu_baseline"], _ = cpu_oracle_sample(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_next_rows(args, A_dev, n, W, store_n, pk, dev):
+    """Throughput of the widened rows on the same grid: the dense bit-stream
+    store (n = 36 bits per solution) of the 2^30 block, against HBM, and the
+    on-device histogram of the first 14 bits over 2^32 solutions."""
+    import torch
+
+    import paper_2103_00693_gb300 as hlf
+
+    hh = hlf.hlf_factor(A_dev, n)
+    dense = torch.empty(hlf.dense_words(store_n, n), dtype=torch.int64, device=dev)
+    hist = torch.empty(1 << 14, dtype=torch.int64, device=dev)
+    hcount = 1 << 32
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    d_ms = timed(lambda: hlf.hlf_enumerate_store_dense(hh, 0, store_n, dense), max(3, args.steps))
+    h_ms = timed(lambda: hlf.hlf_enumerate_histogram(hh, 0, hcount, 0, 14, hist), 3)
+    hlf.hlf_destroy(hh)
+    dbytes = hlf.dense_words(store_n, n) * 8
+    return {"dense_store": {"solutions": store_n, "bits_per_solution": n, "ms_per_launch": d_ms,
+                            "solutions_per_s": store_n / (d_ms / 1e3),
+                            "roofline": {"bound": "hbm", "achieved": dbytes / (d_ms / 1e3) / 1e9,
+                                         "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                         "frac": dbytes / (d_ms / 1e3) / 1e9 / pk["hbm_gbs"]}},
+            "histogram": {"solutions": hcount, "field": "bits 0..13", "ms_per_launch": h_ms,
+                          "solutions_per_s": hcount / (h_ms / 1e3)}}
 
 
 def run_e2e(args, world, dev, A, r, total, store_n, idx_host):

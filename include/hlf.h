@@ -151,12 +151,39 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
                                void* stream);
 
 /*
+ * Stage 2, materialised densely: the same solutions as hlf_enumerate_store,
+ * n bits each, back to back. Solution z(offset + t) occupies bits
+ * [t*n, (t+1)*n) of the stream at out_dev, where stream bit b is bit b % 64
+ * of word b / 64 and solution bit j is z_{j+1}. Bits past the last solution
+ * in the last word are written as 0.
+ * out_dev: device, caller-owned, ceil(count * n / 64) uint64, 8-byte aligned.
+ * Same range rule as hlf_enumerate_store. For n = 36 this writes 36 bits per
+ * solution instead of 64.
+ */
+hlf_status hlf_enumerate_store_dense(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev,
+                                     void* stream);
+
+/*
  * Stage 2, reduced on the device: *red_dev (device, caller-owned, one
  * hlf_reduce) is overwritten with (count, hash sum, XOR-fold) of the window
  * [offset, offset + count). Same range rule as hlf_enumerate_store.
  */
 hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, hlf_reduce* red_dev,
                                 void* stream);
+
+/*
+ * Stage 2, counted into a histogram: hist_dev[v] (device, 2^nbits uint64,
+ * overwritten) is the number of solutions of the window [offset,
+ * offset + count) whose bits bit_lo .. bit_lo + nbits - 1 (bit j is z_{j+1};
+ * bit bit_lo is the least significant bit of v) have value v. These are the
+ * output distributions of the paper's Figs. 3, 6 and 7, where each square
+ * counts one pattern of the first or last bits of z. Requires
+ * 1 <= nbits <= HLF_HIST_MAX_BITS and bit_lo + nbits <= n (else HLF_ERR_ARG);
+ * same range rule as hlf_enumerate_store. No solution is stored.
+ */
+#define HLF_HIST_MAX_BITS 20
+hlf_status hlf_enumerate_histogram(hlf_handle* h, uint64_t offset, uint64_t count, int32_t bit_lo, int32_t nbits,
+                                   uint64_t* hist_dev, void* stream);
 
 /*
  * Stage 2, reduced per chunk: red_dev[c] (device, n_chunks entries) is

@@ -173,3 +173,35 @@ def paper_order(F: Factor, t0: int, count: int) -> np.ndarray:
     _check(_lib().orc_paper_order(_p(F.A, _u8p), _p(F.piv, _i32p), F.r, _p(F.z0, _u8p), F.n,
                                   t0, count, _p(out, _u64p)))
     return out
+
+
+def dense_stream(rows_bits: np.ndarray) -> np.ndarray:
+    """Solutions as one packed bit stream: solution t's bit j is stream bit
+    t * n + j, and stream bit b is bit b % 64 of word b // 64 (LSB first).
+    Bits past the last solution in the last word are 0."""
+    rows_bits = np.asarray(rows_bits, dtype=np.uint8)
+    count, n = rows_bits.shape
+    total = count * n
+    words = (total + 63) // 64
+    flat = np.zeros(words * 64, dtype=np.uint8)
+    flat[:total] = rows_bits.reshape(-1)
+    out = np.zeros(words, dtype=np.uint64)
+    for b in range(64):
+        out |= flat[b::64].astype(np.uint64) << np.uint64(b)
+    return out
+
+
+def window_dense(F: Factor, offset: int, count: int) -> np.ndarray:
+    """The window [offset, offset+count) as a dense bit stream of n bits per
+    solution (see dense_stream)."""
+    return dense_stream(unpack_rows(window(F, offset, count), F.n))
+
+
+def histogram(F: Factor, offset: int, count: int, bit_lo: int, nbits: int, order: str = "gray") -> np.ndarray:
+    """Counts over the window of the value of bits bit_lo .. bit_lo+nbits-1
+    of each solution (bit bit_lo least significant), from the oracle's own
+    window (`order` "gray" or "paper")."""
+    rows = window(F, offset, count) if order == "gray" else paper_order(F, offset, count)
+    bits = unpack_rows(rows, F.n)[:, bit_lo:bit_lo + nbits].astype(np.int64)
+    vals = bits @ (np.int64(1) << np.arange(nbits, dtype=np.int64))
+    return np.bincount(vals, minlength=1 << nbits).astype(np.uint64)

@@ -110,30 +110,31 @@ struct Acc {
 // step between the halves is row L-1, at a compile-time index. `Rows` is a
 // register array (W = 1) or the shared-memory table (W > 1, where register
 // copies of U rows of W words would cost more occupancy than they save).
-template <int W, int L, typename Rows>
+// `Sink` consumes each solution (the reduce accumulator, a histogram).
+template <int W, int L, typename Rows, typename Sink>
 struct GrayBlock {
-    static __device__ __forceinline__ void run(uint64_t (&z)[W], const Rows& Br, Acc<W>& acc)
+    static __device__ __forceinline__ void run(uint64_t (&z)[W], const Rows& Br, Sink& sink)
     {
-        GrayBlock<W, L - 1, Rows>::run(z, Br, acc);
+        GrayBlock<W, L - 1, Rows, Sink>::run(z, Br, sink);
         xor_row<W>(z, Br[L - 1]);
-        GrayBlock<W, L - 1, Rows>::run(z, Br, acc);
+        GrayBlock<W, L - 1, Rows, Sink>::run(z, Br, sink);
     }
 };
-template <int W, typename Rows>
-struct GrayBlock<W, 0, Rows> {
-    static __device__ __forceinline__ void run(uint64_t (&z)[W], const Rows&, Acc<W>& acc) { acc.consume(z); }
+template <int W, typename Rows, typename Sink>
+struct GrayBlock<W, 0, Rows, Sink> {
+    static __device__ __forceinline__ void run(uint64_t (&z)[W], const Rows&, Sink& sink) { sink.consume(z); }
 };
 
 // Walk [i, i + len): consume each solution, step by one row XOR.
-template <int W, int U>
-__device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64_t len, Acc<W>& acc)
+template <int W, int U, typename Sink>
+__device__ __forceinline__ void walk_run(const Table<W>& t, uint64_t i, uint64_t len, Sink& sink)
 {
     if (len == 0) return;
     uint64_t z[W];
     seed<W>(t, i, z);
     constexpr uint64_t kBlk = 1ull << U;
     while (len && (i & (kBlk - 1))) {  // head up to a multiple of 2^U
-        acc.consume(z);
+        sink.consume(z);
         --len;
         ++i;
         if (len) xor_row<W>(z, t.B[ctz64(i)]);
@@ -144,14 +145,14 @@ __device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64
 #pragma unroll
             for (int k = 0; k < U; ++k) Br[k][0] = t.B[k][0];
             do {
-                GrayBlock<W, U, uint64_t[U][W]>::run(z, Br, acc);
+                GrayBlock<W, U, uint64_t[U][W], Sink>::run(z, Br, sink);
                 len -= kBlk;
                 i += kBlk;
                 if (len) xor_row<W>(z, t.B[ctz64(i)]);  // ctz(i) >= U here
             } while (len >= kBlk);
         } else {
             do {
-                GrayBlock<W, U, uint64_t[kTableRows][W]>::run(z, t.B, acc);
+                GrayBlock<W, U, uint64_t[kTableRows][W], Sink>::run(z, t.B, sink);
                 len -= kBlk;
                 i += kBlk;
                 if (len) xor_row<W>(z, t.B[ctz64(i)]);
@@ -159,11 +160,17 @@ __device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64
         }
     }
     while (len) {  // tail
-        acc.consume(z);
+        sink.consume(z);
         --len;
         ++i;
         if (len) xor_row<W>(z, t.B[ctz64(i)]);
     }
+}
+
+template <int W, int U>
+__device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64_t len, Acc<W>& acc)
+{
+    walk_run<W, U, Acc<W>>(t, i, len, acc);
 }
 
 // Block-wide (count, hsum, fold) reduction; the result is valid in thread 0.

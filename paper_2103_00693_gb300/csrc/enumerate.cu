@@ -186,6 +186,20 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const uint64_t* __rest
 // ------------------------------------------------------------- launchers
 
 
+// CTAs of `kernel` that fit on one SM at once (at least 1): grids are sized
+// to one wave, since every kernel here gives its CTAs equal work and a
+// partial second wave would cost a whole extra wave.
+template <typename K>
+int blocks_per_sm(K kernel, size_t smem)
+{
+    int fit = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, kThreads, smem) != cudaSuccess || fit < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return fit;
+}
+
 template <int W>
 hlf_status launch_reduce_w(const uint64_t* table, uint64_t offset, uint64_t count, hlf_reduce* out,
                            cudaStream_t s)
@@ -217,7 +231,7 @@ hlf_status launch_reduce_chunks_w(const uint64_t* table, uint64_t offset, uint64
                                   hlf_reduce* out, cudaStream_t s)
 {
     constexpr int U = unroll_for(W);
-    const uint64_t cap = (uint64_t)sm_count() * 8;
+    const uint64_t cap = (uint64_t)sm_count() * blocks_per_sm(reduce_chunks_kernel<W, U>, 0);
     const unsigned blocks = (unsigned)(n_chunks < cap ? n_chunks : cap);
     reduce_chunks_kernel<W, U><<<blocks, kThreads, 0, s>>>(table, offset, chunk, n_chunks, out);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
@@ -254,7 +268,7 @@ hlf_status launch_store_w(const uint64_t* table, uint64_t offset, uint64_t count
         pl.tail_first = h_end * G;  // wraps to 0 only when the tail is empty
         pl.n_tail = count - pl.n_head - groups * G;
     }
-    const uint64_t max_warps = (uint64_t)sm_count() * 8 * (kThreads / 32);
+    const uint64_t max_warps = (uint64_t)sm_count() * blocks_per_sm(store_kernel<W, S>, 0) * (kThreads / 32);
     const uint64_t min_groups = 64;
     uint64_t warps = (groups + min_groups - 1) / min_groups;
     if (warps > max_warps) warps = max_warps;
@@ -272,7 +286,7 @@ template <int W>
 hlf_status launch_sample_w(const uint64_t* table, int nb, const uint64_t* idx, uint64_t m, uint64_t* out,
                            int32_t* info, cudaStream_t s)
 {
-    const uint64_t cap = (uint64_t)sm_count() * 8;
+    const uint64_t cap = (uint64_t)sm_count() * blocks_per_sm(sample_kernel<W>, 0);
     uint64_t blocks = (m + kThreads - 1) / kThreads;
     if (blocks > cap) blocks = cap;
     sample_kernel<W><<<(unsigned)blocks, kThreads, 0, s>>>(table, nb, idx, m, out, info);

@@ -366,6 +366,22 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
     return after_launch(h, hlf::launch_store(enum_table(h), h->W, offset, count, out_dev, s), s);
 }
 
+hlf_status hlf_enumerate_store_dense(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev,
+                                     void* stream)
+{
+    if (!h || (!out_dev && count)) return HLF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(out_dev) % 8) return HLF_ERR_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return HLF_ERR_CUDA;
+    hlf_status st = ensure_rank(h);
+    if (st != HLF_OK) return st;
+    if (!window_ok(h->r, offset, count)) return HLF_ERR_RANGE;
+    if (count == 0) return HLF_OK;
+    if (count > (~0ull - 63) / (uint64_t)h->n) return HLF_ERR_RANGE;  // stream length in bits
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return after_launch(h, hlf::launch_store_dense(enum_table(h), h->n, offset, count, out_dev, s), s);
+}
+
 hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, hlf_reduce* red_dev, void* stream)
 {
     if (!h || !red_dev) return HLF_ERR_ARG;
@@ -378,6 +394,23 @@ hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, 
     if (cudaMemsetAsync(red_dev, 0, sizeof(hlf_reduce), s) != cudaSuccess) return HLF_ERR_CUDA;
     if (count == 0) return after_launch(h, HLF_OK, s);
     return after_launch(h, hlf::launch_reduce(enum_table(h), h->W, offset, count, red_dev, s), s);
+}
+
+hlf_status hlf_enumerate_histogram(hlf_handle* h, uint64_t offset, uint64_t count, int32_t bit_lo, int32_t nbits,
+                                   uint64_t* hist_dev, void* stream)
+{
+    if (!h || !hist_dev || nbits < 1 || nbits > HLF_HIST_MAX_BITS || bit_lo < 0) return HLF_ERR_ARG;
+    if (bit_lo + nbits > h->n) return HLF_ERR_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return HLF_ERR_CUDA;
+    hlf_status st = ensure_rank(h);
+    if (st != HLF_OK) return st;
+    if (!window_ok(h->r, offset, count)) return HLF_ERR_RANGE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(hist_dev, 0, sizeof(uint64_t) << nbits, s) != cudaSuccess) return HLF_ERR_CUDA;
+    if (count == 0) return after_launch(h, HLF_OK, s);
+    return after_launch(h, hlf::launch_histogram(h->order == HLF_ORDER_PAPER ? h->ptable : h->table, h->W, offset,
+                                                 count, bit_lo, nbits, hist_dev, s), s);
 }
 
 hlf_status hlf_enumerate_reduce_chunks(hlf_handle* h, uint64_t offset, uint64_t chunk, uint64_t n_chunks,

@@ -42,6 +42,10 @@ hlf_status launch_reduce_chunks(const uint64_t* table, int W, uint64_t offset, u
                                 uint64_t n_chunks, hlf_reduce* out, cudaStream_t s);
 hlf_status launch_store(const uint64_t* table, int W, uint64_t offset, uint64_t count,
                         uint64_t* out, cudaStream_t s);
+hlf_status launch_store_dense(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
+                              cudaStream_t s);
+hlf_status launch_histogram(const uint64_t* table, int W, uint64_t offset, uint64_t count, int lo, int nbits,
+                            uint64_t* out, cudaStream_t s);
 hlf_status launch_sample(const uint64_t* table, int W, int nb, const uint64_t* idx, uint64_t m,
                          uint64_t* out, int32_t* info, cudaStream_t s);
 

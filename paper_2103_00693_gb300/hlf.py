@@ -47,8 +47,10 @@ SIGNATURES = {
     "hlf_set_order": (ctypes.c_int, [_vp, _i32]),
     "hlf_get_status": (ctypes.c_int, [_vp]),
     "hlf_enumerate_store": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
+    "hlf_enumerate_store_dense": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_reduce": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_reduce_chunks": (ctypes.c_int, [_vp, _u64, _u64, _u64, _vp, _vp]),
+    "hlf_enumerate_histogram": (ctypes.c_int, [_vp, _u64, _u64, _i32, _i32, _vp, _vp]),
     "hlf_sample": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp]),
     "hlf_destroy": (ctypes.c_int, [_vp]),
     "hlf_many_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp)]),
@@ -209,6 +211,16 @@ def hlf_enumerate_store(h: int, offset: int, count: int, out_dev, stream=None):
                                       _stream_ptr(stream)), "hlf_enumerate_store")
 
 
+def hlf_enumerate_store_dense(h: int, offset: int, count: int, out_dev, stream=None):
+    _check(load().hlf_enumerate_store_dense(h, offset, count, _ptr(out_dev) if out_dev is not None else None,
+                                            _stream_ptr(stream)), "hlf_enumerate_store_dense")
+
+
+def dense_words(count: int, n: int) -> int:
+    """Words of a dense stream of `count` solutions of n bits."""
+    return (count * n + 63) // 64
+
+
 def hlf_enumerate_reduce(h: int, offset: int, count: int, red_dev, stream=None):
     _check(load().hlf_enumerate_reduce(h, offset, count, _ptr(red_dev), _stream_ptr(stream)),
            "hlf_enumerate_reduce")
@@ -218,6 +230,11 @@ def hlf_enumerate_reduce_chunks(h: int, offset: int, chunk: int, n_chunks: int, 
     _check(load().hlf_enumerate_reduce_chunks(h, offset, chunk, n_chunks,
                                               _ptr(red_dev) if red_dev is not None else None,
                                               _stream_ptr(stream)), "hlf_enumerate_reduce_chunks")
+
+
+def hlf_enumerate_histogram(h: int, offset: int, count: int, bit_lo: int, nbits: int, hist_dev, stream=None):
+    _check(load().hlf_enumerate_histogram(h, offset, count, bit_lo, nbits, _ptr(hist_dev), _stream_ptr(stream)),
+           "hlf_enumerate_histogram")
 
 
 def hlf_sample(h: int, idx_dev, m: int, out_dev, stream=None):
@@ -338,6 +355,14 @@ class Factorization:
         hlf_enumerate_store(self.h, offset, count, out, stream)
         return out
 
+    def store_dense(self, offset: int, count: int, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(max(dense_words(count, self.n), 1), dtype=torch.int64, device="cuda")
+        hlf_enumerate_store_dense(self.h, offset, count, out, stream)
+        return out
+
     def reduce(self, offset: int, count: int, red=None, stream=None):
         import torch
 
@@ -353,6 +378,14 @@ class Factorization:
             red = torch.empty((n_chunks, REDUCE_WORDS), dtype=torch.int64, device="cuda")
         hlf_enumerate_reduce_chunks(self.h, offset, chunk, n_chunks, red, stream)
         return red
+
+    def histogram(self, offset: int, count: int, bit_lo: int, nbits: int, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(1 << nbits, dtype=torch.int64, device="cuda")
+        hlf_enumerate_histogram(self.h, offset, count, bit_lo, nbits, out, stream)
+        return out
 
     def sample(self, idx_dev, out=None, stream=None):
         import torch

@@ -1,0 +1,74 @@
+"""The dense bit-stream store (n bits per solution back to back) against the
+oracle's definition of the layout, bit-exact: every word count W = 1..16,
+odd and unaligned offsets, partial last groups, tiny ranks, r > 64, and the
+paper order."""
+
+import numpy as np
+import pytest
+
+import paper_2103_00693_gb300 as hlf
+import synth
+from oracle import cpu as oc
+
+pytestmark = pytest.mark.gpu
+
+
+def _mats():
+    out = [("r0", np.zeros((9, 9), dtype=np.uint8)), ("grid3", synth.grid_instance(3, 0.5, 5)),
+           ("grid6", synth.grid_instance(6, 1.0, 3)), ("grid8", synth.grid_instance(8, 0.5, 0)),
+           ("grid20", synth.grid_instance(20, 0.5, 1234))]
+    for n in (1, 7, 63, 64, 65, 100, 127, 128, 129, 200, 333, 512, 700, 1000, 1024):
+        out.append((f"sym{n}", synth.random_symmetric(n, 0.02, 40 + n)))
+    return out
+
+
+MATS = _mats()
+
+
+@pytest.mark.parametrize("name,A", MATS, ids=[m[0] for m in MATS])
+def test_dense_store(cuda_ok, name, A):
+    import torch
+
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    space = 1 << F.space_log2()
+    cases = [(0, 0), (0, 1), (0, min(space, 64)), (0, min(space, 65)), (1, min(space - 1, 200))]
+    for off, cnt in ((space // 3, 3001), (space - 777, 777), (5, 4096)):
+        off = max(0, min(off, space - 1))
+        cases.append((off, min(cnt, space - off)))
+    for off, cnt in cases:
+        words = hlf.dense_words(cnt, F.n)
+        out = torch.full((words + 2,), -1, dtype=torch.int64, device="cuda")
+        G.store_dense(off, cnt, out)
+        got = out.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got[:words], oc.window_dense(F, off, cnt)), (name, off, cnt)
+        assert np.all(got[words:] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote past the stream"
+    G.close()
+
+
+def test_dense_paper_order(cuda_ok):
+    A = synth.grid_instance(7, 0.5, 77)
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    G.set_order(hlf.ORDER_PAPER)
+    got = G.store_dense(1000, 5000).cpu().numpy().view(np.uint64)
+    want = oc.dense_stream(oc.unpack_rows(oc.paper_order(F, 1000, 5000), F.n))
+    assert np.array_equal(got, want)
+    G.close()
+
+
+def test_dense_grid6_first_2_26(cuda_ok):
+    """The grid6x6 store workload in dense form, 2^26 solutions: sampled
+    blocks against the oracle."""
+    F = oc.factor(synth.grid_instance(6, 1.0, 3))
+    G = hlf.Factorization.from_dense(synth.grid_instance(6, 1.0, 3))
+    cnt = 1 << 26
+    out = G.store_dense(0, cnt).cpu().numpy().view(np.uint64)
+    assert len(out) == cnt * 36 // 64
+    rng = np.random.default_rng(3)
+    for s in [0, cnt - 1024] + list(rng.integers(0, cnt // 1024 - 1, size=32) * 1024):
+        s = int(s)
+        want = oc.window_dense(F, s, 1024)  # 1024 * 36 bits = 576 whole words
+        w0 = s * 36 // 64
+        assert np.array_equal(out[w0:w0 + len(want)], want), s
+    G.close()

@@ -301,3 +301,48 @@ def test_paper_order_beyond_64_pivots():
         par = (Z @ F.X.T.astype(np.int64)) % 2
         assert np.array_equal(par, np.broadcast_to(F.q // 2, par.shape))
         assert len({tuple(z) for z in Z}) == cnt
+
+
+def test_dense_stream_layout():
+    """The dense layout, checked bit by bit from its definition."""
+    rng = np.random.default_rng(2)
+    for count, n in ((1, 1), (3, 9), (64, 36), (65, 36), (7, 64), (5, 65), (9, 130)):
+        rows = (rng.random((count, n)) < 0.5).astype(np.uint8)
+        s = oc.dense_stream(rows)
+        assert len(s) == (count * n + 63) // 64
+        for t in range(count):
+            for j in range(n):
+                b = t * n + j
+                assert (int(s[b // 64]) >> (b % 64)) & 1 == rows[t, j]
+        tail = count * n
+        if tail % 64:
+            assert int(s[-1]) >> (tail % 64) == 0
+
+
+def _gf2_rank(rows: np.ndarray) -> int:
+    """Rank over GF(2) of 0/1 rows, by brute force over subsets for tiny
+    inputs (independent of the oracle's elimination)."""
+    rows = [int("".join(map(str, r[::-1])), 2) for r in rows]
+    span = {0}
+    for v in rows:
+        span |= {s ^ v for s in span}
+    return len(span).bit_length() - 1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_histogram_closed_form(seed):
+    """Over the full solution set (an affine space of dimension r), the
+    values of any bit field form an affine space of dimension d = rank of
+    the basis restricted to those bits, each value hit exactly 2^(r-d)
+    times (Sec. 2: the solutions are z^a + Col(A))."""
+    A = synth.grid_instance(4, 0.5, 900 + seed)
+    F = oc.factor(A)
+    for lo, nb in ((0, 4), (3, 5), (F.n - 6, 6), (0, F.n)):
+        h = oc.histogram(F, 0, 1 << F.r, lo, nb)
+        d = _gf2_rank(F.basis[:, lo:lo + nb])
+        nz = h[h > 0]
+        assert len(nz) == 1 << d and np.all(nz == (1 << (F.r - d)))
+        z0v = int(sum(int(F.z0[lo + j]) << j for j in range(nb)))
+        assert h[z0v] > 0
+    # paper order gives the same histogram over the full set
+    assert np.array_equal(oc.histogram(F, 0, 1 << F.r, 2, 7), oc.histogram(F, 0, 1 << F.r, 2, 7, "paper"))

@@ -15,6 +15,7 @@ from .grid import (  # noqa: F401
     grid_instance,
     paper_b_patterns,
     poisson_stream,
+    random_regular,
     random_symmetric,
     sample_indices,
     window_offset,

@@ -101,6 +101,39 @@ def random_symmetric(n: int, density: float, seed: int) -> np.ndarray:
     return A
 
 
+def random_regular(n: int, d: int, seed: int, *, b=None) -> np.ndarray:
+    """A random simple d-regular graph on n vertices (§5: any symmetric A),
+    drawn by sequential pairing: n*d points (d per vertex) are matched two at
+    a time at random, a pair that would make a loop or a repeated edge is
+    redrawn, and a dead end restarts the draw. The diagonal is Bernoulli(1/2)
+    unless b is given."""
+    if (n * d) % 2 or d >= n:
+        raise ValueError("need n*d even and d < n")
+    rng = _rng(seed)
+    for _ in range(1000):
+        pts = list(np.repeat(np.arange(n), d))
+        edges = set()
+        ok = True
+        while pts:
+            for _ in range(200):
+                i, j = rng.integers(0, len(pts), size=2)
+                u, v = int(pts[i]), int(pts[j])
+                if i != j and u != v and (min(u, v), max(u, v)) not in edges:
+                    break
+            else:
+                ok = False
+                break
+            edges.add((min(u, v), max(u, v)))
+            for k in sorted((int(i), int(j)), reverse=True):
+                pts[k] = pts[-1]
+                pts.pop()
+        if ok:
+            if b is None:
+                b = (rng.random(n) < 0.5).astype(np.uint8)
+            return _assemble(n, sorted(edges), b)
+    raise RuntimeError("could not draw a simple regular graph")
+
+
 def window_offset(seed: int, space_log2: int, count: int) -> int:
     """A window start drawn uniformly from [0, 2^space_log2 - count]; the
     caller passes space_log2 = min(r, 64) and a count that fits."""

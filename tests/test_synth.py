@@ -49,3 +49,12 @@ def test_batch_and_stream_generators():
     ts = [r["t_arrival"] for r in reqs]
     assert ts == sorted(ts) and ts[0] == 0.0
     assert all((1 << 10) <= r["want"] <= (1 << 24) for r in reqs)
+
+
+def test_random_regular_graphs():
+    for n, d in ((10, 3), (64, 4), (1024, 3), (500, 8)):
+        A = synth.random_regular(n, d, 7)
+        off = A.copy()
+        off[np.arange(n), np.arange(n)] = 0
+        assert np.array_equal(A, A.T)
+        assert np.all(off.sum(axis=1) == d)

@@ -105,3 +105,53 @@ def per_instance(mats: list[np.ndarray], cap: int, device: str = "cuda"):
         hlf.hlf_enumerate_reduce(h, 0, total, red[b])
         hlf.hlf_destroy(h)
     return ranks, red
+
+
+def main(argv=None):
+    """Run the batched workload (or its first `--count` grids) once and
+    print launch time and throughput; `--tiles CTAS CHUNK` skips the
+    autotuner."""
+    import argparse
+    import time
+
+    import torch
+
+    from synth import workloads as wl
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--cap-log2", type=int, default=wl.BATCH_CAP_LOG2)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tiles", type=int, nargs=2, default=None)
+    a = ap.parse_args(argv)
+    mats = wl.batch()[: a.count]
+    cap = 1 << a.cap_log2
+    B = Batch(mats)
+    if a.tiles:
+        B.set_tiles(a.tiles[0], a.tiles[1])
+    else:
+        from . import autotune
+
+        autotune.autotune(B, cap, reps=1)
+    B.run(cap)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.reps):
+        B.run(cap)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / a.reps
+    st = B.status()
+    r, red = B.results()
+    sols = sum(x.count for x in red)
+    print(f"{len(mats)} grids, tiles {B.tiles}: {1e3 * dt:.3f} ms/launch, {len(mats) / dt:.3e} inst/s, "
+          f"{sols / dt:.3e} solutions/s, status {st}")
+    B.close()
+    return 0 if st == 0 else 1
+
+
+if __name__ == "__main__":
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    raise SystemExit(main())

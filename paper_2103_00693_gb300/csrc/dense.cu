@@ -3,19 +3,34 @@
 // instead of W whole words. For n = 36 that is 36 bits instead of 64 per
 // solution. The solutions are those of hlf_enumerate_store.
 //
-// A warp produces 64 consecutive solutions per step; 64 solutions of n bits
-// are exactly n words, so every group's words start on a word boundary for
-// any n. Each lane walks two Gray chains (relative positions 2*lane and
-// 2*lane+1 of the group) that advance by 64 in absolute index per step:
-// with i = 64 H + l, z(i + 64) = z(i) ^ B_5 ^ B_{6 + ctz(H + 1)} (the
-// lane-interleaved identity of enumerate.cu), so a step is one row XOR per
-// solution whatever the window's offset. The group's 64 solutions are
-// staged in shared memory; output word j of a group holds stream bits
-// [64 j, 64 j + 64), which start at bit o of solution s, with (s, o) taken
-// from a per-CTA table built once (no division in the loop). Each lane
-// assembles whole output words with shifts (at n <= 64: one word of solution
-// s, then the next solutions shifted in), and the warp writes the group's n
-// words out, coalesced.
+// n < 64 (one word per row), dense1_kernel: a lane owns a run of M
+// consecutive solutions whose bits fill whole words, M*n being a multiple of
+// 64 (M = max(64 / gcd(n, 64), 16)). Every run therefore starts on a word
+// boundary and solution t of a run sits at bit (t*n) mod 64 of its word in
+// every lane alike, so the lanes append their solutions to a two-word bit
+// buffer in lockstep and stage each completed word in shared memory; after 32
+// runs (one per lane, a "pass") the warp copies the pass's 32*M*n/64 words
+// out, coalesced. Inside a run, solution t+1 is solution t XOR B_ctz(i+1);
+// that row index depends only on i mod M except at the one step of a run
+// where i+1 is a multiple of M, so every other step uses a row shared by all
+// lanes (compile-time registers when the window offset is a multiple of M, a
+// shared-memory table otherwise). From one pass to the next a lane's run
+// start x advances by 32*M = 2^b, and g(x) ^ g(x + 2^b) has exactly bits b-1
+// and c, c = b + (number of trailing ones of x >> b): two row XORs.
+//
+// n = 64 with a 16-byte aligned output is the packed store itself; otherwise
+// (n >= 64), dense_kernel: a warp produces 64
+// consecutive solutions per step; 64 solutions of n bits are exactly n words,
+// so every group's words start on a word boundary for any n. Each lane walks
+// two Gray chains (relative positions 2*lane and 2*lane+1 of the group) that
+// advance by 64 in absolute index per step: with i = 64 H + l,
+// z(i + 64) = z(i) ^ B_5 ^ B_{6 + ctz(H + 1)} (the lane-interleaved identity
+// of enumerate.cu), so a step is one row XOR per solution whatever the
+// window's offset. The group's 64 solutions are staged in shared memory;
+// output word j of a group holds stream bits [64 j, 64 j + 64), which start
+// at bit o of solution s, with (s, o) taken from a per-CTA table built once
+// (no division in the loop). Each lane assembles whole output words with
+// shifts, and the warp writes the group's n words out, coalesced.
 
 #include "enum_impl.cuh"
 
@@ -122,6 +137,169 @@ __global__ void __launch_bounds__(kThreads) dense_kernel(const uint64_t* __restr
     }
 }
 
+// ------------------------------------------------------------ n < 64
+constexpr int kD1Threads = 256;
+constexpr int kD1Warps = kD1Threads / 32;
+
+struct Dense1Plan {
+    uint64_t offset, count;
+    uint64_t passes;    // ceil(count / (32 M)); a pass is 32 runs of M solutions
+    uint64_t full;      // passes whose 32 runs are all inside the window
+    uint64_t per_warp;  // consecutive passes per warp
+    uint64_t words;     // ceil(count * n / 64), the stream's length in words
+    int n, wpr;         // wpr = M * n / 64 words per run
+};
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// Step t of a lane's run (t = T, a compile-time constant, so that the
+// aligned walk's row index ctz(T + 1) selects a register): append solution
+// z to the bit buffer (lo, fill), stage a completed word at mine[w], then
+// step z to solution T + 1.
+template <int M, int T, bool Aligned, bool Tail>
+struct Dense1Step {
+    static __device__ __forceinline__ void go(uint64_t& z, uint64_t& lo, int& fill, int& w, uint64_t valid, int n,
+                                              const uint64_t* s_step, const uint64_t (&Breg)[ilog2(M)], int tstar,
+                                              uint64_t sp, uint64_t* mine)
+    {
+        const uint64_t v = (Tail && (uint64_t)T >= valid) ? 0ull : z;
+        lo |= v << fill;
+        if (fill + n >= 64) {  // the same in every lane
+            mine[w++] = lo;
+            lo = fill ? v >> (64 - fill) : 0ull;
+            fill += n - 64;
+        } else {
+            fill += n;
+        }
+        if constexpr (T + 1 < M) {
+            if constexpr (Aligned) {
+                constexpr int k = ilog2((T + 1) & -(T + 1));  // ctz(T + 1)
+                z ^= Breg[k];
+            } else {
+                z ^= s_step[T];
+                if (T == tstar) z ^= sp;
+            }
+            Dense1Step<M, T + 1, Aligned, Tail>::go(z, lo, fill, w, valid, n, s_step, Breg, tstar, sp, mine);
+        }
+    }
+};
+
+// One lane's run of M solutions starting at absolute index i0 (solution z):
+// the wpr completed words go to `mine`. Tail: solutions t >= valid are
+// outside the window and contribute zero bits.
+template <int M, bool Aligned, bool Tail>
+__device__ __forceinline__ void dense1_run(uint64_t z, uint64_t i0, uint64_t valid, int n,
+                                           const uint64_t* s_B, const uint64_t* s_step,
+                                           const uint64_t (&Breg)[ilog2(M)], int tstar, uint64_t* mine)
+{
+    uint64_t sp = 0;  // the lane's own row at the step where i0 + t + 1 is a multiple of M
+    if constexpr (!Aligned) sp = s_B[ctz64(i0 + (uint64_t)tstar + 1)];
+    uint64_t lo = 0;
+    int fill = 0, w = 0;
+    Dense1Step<M, 0, Aligned, Tail>::go(z, lo, fill, w, valid, n, s_step, Breg, tstar, sp, mine);
+}
+
+template <int M, bool Aligned>
+__global__ void __launch_bounds__(kD1Threads) dense1_kernel(const uint64_t* __restrict__ table, Dense1Plan pl,
+                                                            uint64_t* __restrict__ out)
+{
+    constexpr int A = ilog2(M);
+    constexpr int b = A + 5;  // a pass advances every run start by 32 M = 2^b
+    extern __shared__ __align__(16) uint64_t s_stage[];  // [warps][32 * wpr]
+    __shared__ uint64_t s_B[kTableRows];
+    __shared__ uint64_t s_step[M];
+    __shared__ uint64_t s_z0;
+    for (int k = threadIdx.x; k < kTableRows; k += blockDim.x) s_B[k] = table[k];
+    if (threadIdx.x == 0) s_z0 = table[kTableZ0Row];
+    const uint32_t off_low = (uint32_t)pl.offset & (M - 1);
+    __syncthreads();
+    if constexpr (!Aligned) {
+        for (int t = threadIdx.x; t < M; t += blockDim.x) {
+            const uint32_t u = (off_low + (uint32_t)t + 1) & (M - 1);
+            s_step[t] = u ? s_B[__ffs(u) - 1] : 0ull;
+        }
+        __syncthreads();
+    }
+    const int tstar = Aligned ? M : (int)(M - 1 - off_low);
+    uint64_t Breg[A];
+#pragma unroll
+    for (int k = 0; k < A; ++k) Breg[k] = s_B[k];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t gw = (uint64_t)blockIdx.x * kD1Warps + warp;
+    const uint64_t P0 = gw * pl.per_warp;
+    if (P0 >= pl.passes) return;
+    const uint64_t P1 = min(P0 + pl.per_warp, pl.passes);
+    const int n = pl.n;
+    const uint64_t pass_words = 32ull * (uint64_t)pl.wpr;
+    uint64_t* stage = s_stage + (size_t)warp * pass_words;
+    uint64_t* mine = stage + (size_t)lane * pl.wpr;
+
+    uint64_t j0 = (P0 * 32 + (uint64_t)lane) * M;  // run start, relative to the window
+    uint64_t i0 = pl.offset + j0;                  // and absolute
+    uint64_t zs = s_z0;
+    for (uint64_t g = i0 ^ (i0 >> 1); g; g &= g - 1) zs ^= s_B[__ffsll((long long)g) - 1];
+
+    for (uint64_t P = P0;;) {
+        if (P < pl.full) {
+            dense1_run<M, Aligned, false>(zs, i0, M, n, s_B, s_step, Breg, tstar, mine);
+        } else {
+            const uint64_t valid = j0 < pl.count ? min(pl.count - j0, (uint64_t)M) : 0;
+            dense1_run<M, Aligned, true>(zs, i0, valid, n, s_B, s_step, Breg, tstar, mine);
+        }
+        __syncwarp();
+        const uint64_t w0 = P * pass_words;
+        const int nw = (int)min(pass_words, pl.words - w0);
+        for (int q = lane; q < nw; q += 32) st_cs(out + w0 + q, stage[q]);
+        __syncwarp();
+        if (++P == P1) break;
+        const int c = b + ctz64(~(i0 >> b));  // <= 64: the top b bits of i0 >> b are 0
+        zs ^= s_B[b - 1] ^ s_B[c];
+        i0 += 32ull * M;
+        j0 += 32ull * M;
+    }
+}
+
+template <int M, bool Aligned>
+hlf_status launch_dense1(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
+                         cudaStream_t s)
+{
+    constexpr uint64_t per_pass = 32ull * M;
+    Dense1Plan pl{};
+    pl.offset = offset;
+    pl.count = count;
+    pl.n = n;
+    pl.wpr = M * n / 64;
+    pl.full = count / per_pass;
+    pl.passes = pl.full + (count % per_pass != 0);
+    pl.words = (count * (uint64_t)n + 63) / 64;  // count * n <= 2^64 - 64 (checked by the caller)
+    const size_t smem = (size_t)kD1Warps * 32 * pl.wpr * sizeof(uint64_t);
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        const int most = kD1Warps * 32 * (M * 63 / 64) * (int)sizeof(uint64_t);  // n <= 63
+        if (cudaFuncSetAttribute(dense1_kernel<M, Aligned>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
+            cudaSuccess)
+            return HLF_ERR_CUDA;
+        attr_set[dev] = true;
+    }
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense1_kernel<M, Aligned>, kD1Threads, smem) !=
+        cudaSuccess)
+        return HLF_ERR_CUDA;
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t max_warps = (uint64_t)sm_count() * per_sm * kD1Warps;
+    const uint64_t warps = pl.passes < max_warps ? pl.passes : max_warps;
+    pl.per_warp = (pl.passes + warps - 1) / warps;
+    const uint64_t used = (pl.passes + pl.per_warp - 1) / pl.per_warp;
+    const unsigned blocks = (unsigned)((used + kD1Warps - 1) / kD1Warps);
+    dense1_kernel<M, Aligned><<<blocks, kD1Threads, smem, s>>>(table, pl, out);
+    return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ n >= 64
 template <int W>
 hlf_status launch_dense_w(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
                           cudaStream_t s)
@@ -164,6 +342,21 @@ hlf_status launch_dense_w(const uint64_t* table, int n, uint64_t offset, uint64_
 hlf_status launch_store_dense(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
                               cudaStream_t s)
 {
+    if (n < 64) {
+        const int m = 64 / (n & -n);  // 64 / gcd(n, 64)
+        const int M = m < 16 ? 16 : m;
+        const bool aligned = (offset & (uint64_t)(M - 1)) == 0;
+        switch (M) {
+        case 16: return aligned ? launch_dense1<16, true>(table, n, offset, count, out, s)
+                                : launch_dense1<16, false>(table, n, offset, count, out, s);
+        case 32: return aligned ? launch_dense1<32, true>(table, n, offset, count, out, s)
+                                : launch_dense1<32, false>(table, n, offset, count, out, s);
+        default: return aligned ? launch_dense1<64, true>(table, n, offset, count, out, s)
+                                : launch_dense1<64, false>(table, n, offset, count, out, s);
+        }
+    }
+    if (n == 64 && reinterpret_cast<uintptr_t>(out) % 16 == 0)  // one whole word per solution
+        return launch_store(table, 1, offset, count, out, s);
     switch ((n + 63) / 64) {
     case 1: return launch_dense_w<1>(table, n, offset, count, out, s);
     case 2: return launch_dense_w<2>(table, n, offset, count, out, s);

@@ -72,3 +72,33 @@ def test_dense_grid6_first_2_26(cuda_ok):
         w0 = s * 36 // 64
         assert np.array_equal(out[w0:w0 + len(want)], want), s
     G.close()
+
+
+@pytest.mark.parametrize("n", list(range(1, 65)))
+def test_dense_one_word_rows(cuda_ok, n):
+    """n <= 64, every n: lane runs of M = max(64 / gcd(n, 64), 16) solutions
+    (16, 32 or 64), window offsets that are and are not multiples of M, a
+    single solution, ragged last passes, and windows long enough that each
+    warp walks several passes. For n = 64, an output that is 16-byte aligned
+    (the packed store) and one that is only 8-byte aligned."""
+    import torch
+
+    A = synth.random_symmetric(n, 0.3, 100 + n)
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    space = 1 << F.space_log2()
+    for k, cnt in enumerate((1, 511, 2049, 70001)):
+        cnt = min(cnt, space)
+        for aligned in (True, False):
+            off = synth.window_offset(100 * n + k, F.space_log2(), cnt)
+            off = off & ~63 if aligned else off | 1
+            off = min(off, space - cnt)
+            words = hlf.dense_words(cnt, n)
+            for lead in ((0, 1) if n == 64 else (0,)):
+                buf = torch.full((words + 3,), -1, dtype=torch.int64, device="cuda")
+                G.store_dense(off, cnt, buf[lead:])
+                got = buf.cpu().numpy().view(np.uint64)
+                assert np.array_equal(got[lead:lead + words], oc.window_dense(F, off, cnt)), (off, cnt, lead)
+                assert np.all(got[lead + words:] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote past the stream"
+                assert np.all(got[:lead] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote before the stream"
+    G.close()

@@ -152,25 +152,47 @@ struct Dense1Plan {
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
+// Shifts with PTX semantics: amounts of 64 give 0 (no special case for an
+// empty bit buffer).
+__device__ __forceinline__ uint64_t shl64(uint64_t x, uint32_t s)
+{
+    uint64_t r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+__device__ __forceinline__ uint64_t shr64(uint64_t x, uint32_t s)
+{
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+// Predicated shared-memory store (no branch around it).
+__device__ __forceinline__ void st_shared_if(bool p, uint64_t* a, uint64_t v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.u64 [%1], %2;\n\t}" ::"r"((uint32_t)p),
+                 "r"((uint32_t)__cvta_generic_to_shared(a)), "l"(v)
+                 : "memory");
+}
+
 // Step t of a lane's run (t = T, a compile-time constant, so that the
 // aligned walk's row index ctz(T + 1) selects a register): append solution
 // z to the bit buffer (lo, fill), stage a completed word at mine[w], then
-// step z to solution T + 1.
+// step z to solution T + 1. Everything that depends on the bit position is
+// the same in every lane, and the word is staged by a predicated store.
 template <int M, int T, bool Aligned, bool Tail>
 struct Dense1Step {
-    static __device__ __forceinline__ void go(uint64_t& z, uint64_t& lo, int& fill, int& w, uint64_t valid, int n,
-                                              const uint64_t* s_step, const uint64_t (&Breg)[ilog2(M)], int tstar,
-                                              uint64_t sp, uint64_t* mine)
+    static __device__ __forceinline__ void go(uint64_t& z, uint64_t& lo, uint32_t& fill, uint32_t& w, uint64_t valid,
+                                              uint32_t n, const uint64_t* s_step, const uint64_t (&Breg)[ilog2(M)],
+                                              int tstar, uint64_t sp, uint64_t* mine)
     {
         const uint64_t v = (Tail && (uint64_t)T >= valid) ? 0ull : z;
-        lo |= v << fill;
-        if (fill + n >= 64) {  // the same in every lane
-            mine[w++] = lo;
-            lo = fill ? v >> (64 - fill) : 0ull;
-            fill += n - 64;
-        } else {
-            fill += n;
-        }
+        lo |= shl64(v, fill);
+        const bool full = fill + n >= 64;
+        st_shared_if(full, mine + w, lo);
+        const uint64_t carry = shr64(v, 64 - fill);  // bits of v past the word; 0 when fill == 0
+        lo = full ? carry : lo;
+        w += full;
+        fill = full ? fill + n - 64 : fill + n;
         if constexpr (T + 1 < M) {
             if constexpr (Aligned) {
                 constexpr int k = ilog2((T + 1) & -(T + 1));  // ctz(T + 1)
@@ -195,12 +217,12 @@ __device__ __forceinline__ void dense1_run(uint64_t z, uint64_t i0, uint64_t val
     uint64_t sp = 0;  // the lane's own row at the step where i0 + t + 1 is a multiple of M
     if constexpr (!Aligned) sp = s_B[ctz64(i0 + (uint64_t)tstar + 1)];
     uint64_t lo = 0;
-    int fill = 0, w = 0;
-    Dense1Step<M, 0, Aligned, Tail>::go(z, lo, fill, w, valid, n, s_step, Breg, tstar, sp, mine);
+    uint32_t fill = 0, w = 0;
+    Dense1Step<M, 0, Aligned, Tail>::go(z, lo, fill, w, valid, (uint32_t)n, s_step, Breg, tstar, sp, mine);
 }
 
 template <int M, bool Aligned>
-__global__ void __launch_bounds__(kD1Threads) dense1_kernel(const uint64_t* __restrict__ table, Dense1Plan pl,
+__global__ void __launch_bounds__(kD1Threads, M == 64 ? 3 : 4) dense1_kernel(const uint64_t* __restrict__ table, Dense1Plan pl,
                                                             uint64_t* __restrict__ out)
 {
     constexpr int A = ilog2(M);

@@ -223,6 +223,46 @@ __device__ __forceinline__ void st_cs(uint64_t* p, uint64_t a)
     asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(a) : "memory");
 }
 
+// 32 consecutive solutions of W > 1 words, one per lane (lane l holds the
+// solution whose W words start at dst + l*W), written out coalesced: each lane
+// stages its words in shared memory with an odd row stride (W | 1, so the
+// lane-strided writes of one word index fall in distinct banks), then
+// consecutive lanes store consecutive words of the 32*W-word block. `stage`
+// holds 32*(W|1) words for this warp. With W even, dst must be 16-byte
+// aligned and each lane stores word pairs.
+template <int W>
+constexpr int stage_words()
+{
+    return 32 * (W | 1);
+}
+
+template <int W, bool Pairs>
+__device__ __forceinline__ void store_warp_coalesced(uint64_t* dst, const uint64_t (&z)[W], uint64_t* stage,
+                                                     int lane)
+{
+    static_assert(W > 1, "W = 1 stores pairs of solutions straight from registers");
+    constexpr int SW = W | 1;
+#pragma unroll
+    for (int w = 0; w < W; ++w) stage[lane * SW + w] = z[w];
+    __syncwarp();
+    if constexpr (Pairs && W % 2 == 0) {
+#pragma unroll 4
+        for (int k = 0; k < W / 2; ++k) {
+            const int q = 2 * (lane + 32 * k);  // even, so q % W is even and q, q + 1 share a row
+            const int l = q / W, w = q - l * W;
+            st_cs_v2(dst + q, stage[l * SW + w], stage[l * SW + w + 1]);
+        }
+    } else {
+#pragma unroll 4
+        for (int k = 0; k < W; ++k) {
+            const int q = lane + 32 * k;
+            const int l = q / W, w = q - l * W;
+            st_cs(dst + q, stage[l * SW + w]);
+        }
+    }
+    __syncwarp();  // the stage is rewritten by the next call
+}
+
 template <int W>
 __device__ __forceinline__ void store_one(uint64_t* p, const uint64_t (&z)[W])
 {

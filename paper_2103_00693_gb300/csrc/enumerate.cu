@@ -23,7 +23,10 @@
 //                        so stepping h -> h+1 XORs the same row
 //                        C_j = B_{m-1} ^ B_{m+j}, j = ctz(h+1), into every
 //                        lane: one XOR per solution and a warp writes G
-//                        consecutive solutions per step (512 B at W = 1).
+//                        consecutive solutions per step (512 B at W = 1;
+//                        at W > 1 the lanes' solutions are restaged in
+//                        shared memory so that the warp writes its 32*W
+//                        words with consecutive lanes on consecutive words).
 //   sample_kernel        z(i) at arbitrary indices, straight from the formula.
 
 #include "enum_impl.cuh"
@@ -112,6 +115,7 @@ __global__ void __launch_bounds__(kThreads) store_kernel(const uint64_t* __restr
 {
     constexpr int G = 32 * S;
     constexpr int M = (S == 2) ? 6 : 5;  // log2 G
+    extern __shared__ __align__(16) uint64_t s_stage[];  // W > 1: [warps][stage_words<W>()]
     __shared__ Table<W> t;
     __shared__ uint64_t s_C[kTableRows - M][W];  // C_j = B_{M-1} ^ B_{M+j}
     load_table<W>(t, table);
@@ -141,8 +145,8 @@ __global__ void __launch_bounds__(kThreads) store_kernel(const uint64_t* __restr
     seed<W>(t, h0 * G + (uint64_t)(S * lane), z);
     const bool even = (pl.offset & 1) == 0;
     for (uint64_t h = h0;;) {
-        uint64_t* p = out + (h * G + (uint64_t)(S * lane) - pl.offset) * W;
         if constexpr (S == 2) {
+            uint64_t* p = out + (h * G + (uint64_t)(S * lane) - pl.offset) * W;
             const uint64_t z1 = z[0] ^ t.B[0][0];  // g(2t+1) = g(2t) ^ 1
             if (even) {
                 st_cs_v2(p, z[0], z1);
@@ -150,8 +154,9 @@ __global__ void __launch_bounds__(kThreads) store_kernel(const uint64_t* __restr
                 st_cs(p, z[0]);
                 st_cs(p + 1, z1);
             }
-        } else {
-            store_one<W>(p, z);
+        } else {  // out is 16-byte aligned (checked by the caller)
+            store_warp_coalesced<W, true>(out + (h * G - pl.offset) * W, z,
+                                          s_stage + (threadIdx.x >> 5) * stage_words<W>(), lane);
         }
         if (++h == h1) break;
         xor_row<W>(z, s_C[ctz64(h)]);
@@ -268,7 +273,19 @@ hlf_status launch_store_w(const uint64_t* table, uint64_t offset, uint64_t count
         pl.tail_first = h_end * G;  // wraps to 0 only when the tail is empty
         pl.n_tail = count - pl.n_head - groups * G;
     }
-    const uint64_t max_warps = (uint64_t)sm_count() * blocks_per_sm(store_kernel<W, S>, 0) * (kThreads / 32);
+    const size_t smem = S == 1 ? (size_t)(kThreads / 32) * stage_words<W>() * sizeof(uint64_t) : 0;
+    if (S == 1) {
+        static bool attr_set[64] = {false};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !attr_set[dev]) {
+            if (cudaFuncSetAttribute(store_kernel<W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return HLF_ERR_CUDA;
+            attr_set[dev] = true;
+        }
+    }
+    const uint64_t max_warps = (uint64_t)sm_count() * blocks_per_sm(store_kernel<W, S>, smem) * (kThreads / 32);
     const uint64_t min_groups = 64;
     uint64_t warps = (groups + min_groups - 1) / min_groups;
     if (warps > max_warps) warps = max_warps;
@@ -278,7 +295,7 @@ hlf_status launch_store_w(const uint64_t* table, uint64_t offset, uint64_t count
     uint64_t threads = warps * 32;
     if (threads < ragged) threads = ragged;
     const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
-    store_kernel<W, S><<<blocks, kThreads, 0, s>>>(table, pl, out);
+    store_kernel<W, S><<<blocks, kThreads, smem, s>>>(table, pl, out);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 

@@ -8,7 +8,9 @@
 // multiple of G, seeded one by one from the definition), the other tasks
 // cover runs of up to kTaskGroups aligned groups of G consecutive indices
 // with the lane-interleaved Gray identity of enumerate.cu (one row XOR per
-// solution, a warp writes G consecutive solutions per step). Warps take tasks
+// solution, a warp writes G consecutive solutions per step; solutions of
+// W > 1 words are restaged in shared memory so that the warp's stores are
+// coalesced). Warps take tasks
 // grid-stride and find their window by binary search over the task prefix
 // sums. The basis rows are read through the read-only cache: every lane of a
 // warp reads the same row, so each load is one broadcast.
@@ -47,7 +49,7 @@ __device__ __forceinline__ void seed_g(const uint64_t* __restrict__ tab, uint64_
 }
 
 template <int W>
-__device__ void many_task(const WinDesc& d, uint64_t u, int lane)
+__device__ void many_task(const WinDesc& d, uint64_t u, int lane, uint64_t* stage)
 {
     constexpr int S = (W == 1) ? 2 : 1;
     constexpr uint64_t G = 32 * S;
@@ -68,10 +70,10 @@ __device__ void many_task(const WinDesc& d, uint64_t u, int lane)
     const uint64_t h1 = min(h0 + kTaskGroups, d.h_end);
     uint64_t z[W];
     seed_g<W>(d.table, h0 * G + (uint64_t)(S * lane), z);
-    const bool even = (d.offset & 1) == 0;
+    const bool even = (d.offset & 1) == 0;  // outputs are 16-byte aligned (checked by the caller)
     for (uint64_t h = h0;;) {
-        uint64_t* p = d.out + (h * G + (uint64_t)(S * lane) - d.offset) * W;
         if constexpr (S == 2) {
+            uint64_t* p = d.out + (h * G + (uint64_t)(S * lane) - d.offset) * W;
             const uint64_t z1 = z[0] ^ __ldg(d.table);  // g(2t+1) = g(2t) ^ 1
             if (even) {
                 st_cs_v2(p, z[0], z1);
@@ -80,7 +82,7 @@ __device__ void many_task(const WinDesc& d, uint64_t u, int lane)
                 st_cs(p + 1, z1);
             }
         } else {
-            store_one<W>(p, z);
+            store_warp_coalesced<W, true>(d.out + (h * G - d.offset) * W, z, stage, lane);
         }
         if (++h == h1) break;
         const int j = ctz64(h);
@@ -89,8 +91,10 @@ __device__ void many_task(const WinDesc& d, uint64_t u, int lane)
     }
 }
 
-__global__ void __launch_bounds__(kThreads) many_kernel(const WinDesc* __restrict__ d, int k, uint64_t total_tasks)
+__global__ void __launch_bounds__(kThreads, 2) many_kernel(const WinDesc* __restrict__ d, int k, uint64_t total_tasks)
 {
+    extern __shared__ __align__(16) uint64_t s_stage[];  // [warps][stage_words<16>()]
+    uint64_t* stage = s_stage + (threadIdx.x >> 5) * stage_words<HLF_MAX_W>();
     const int lane = threadIdx.x & 31;
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total_tasks; t += nwarps) {
@@ -103,22 +107,22 @@ __global__ void __launch_bounds__(kThreads) many_kernel(const WinDesc* __restric
         const WinDesc& w = d[lo];
         const uint64_t u = t - w.task_base;
         switch (w.W) {
-        case 1: many_task<1>(w, u, lane); break;
-        case 2: many_task<2>(w, u, lane); break;
-        case 3: many_task<3>(w, u, lane); break;
-        case 4: many_task<4>(w, u, lane); break;
-        case 5: many_task<5>(w, u, lane); break;
-        case 6: many_task<6>(w, u, lane); break;
-        case 7: many_task<7>(w, u, lane); break;
-        case 8: many_task<8>(w, u, lane); break;
-        case 9: many_task<9>(w, u, lane); break;
-        case 10: many_task<10>(w, u, lane); break;
-        case 11: many_task<11>(w, u, lane); break;
-        case 12: many_task<12>(w, u, lane); break;
-        case 13: many_task<13>(w, u, lane); break;
-        case 14: many_task<14>(w, u, lane); break;
-        case 15: many_task<15>(w, u, lane); break;
-        default: many_task<16>(w, u, lane); break;
+        case 1: many_task<1>(w, u, lane, stage); break;
+        case 2: many_task<2>(w, u, lane, stage); break;
+        case 3: many_task<3>(w, u, lane, stage); break;
+        case 4: many_task<4>(w, u, lane, stage); break;
+        case 5: many_task<5>(w, u, lane, stage); break;
+        case 6: many_task<6>(w, u, lane, stage); break;
+        case 7: many_task<7>(w, u, lane, stage); break;
+        case 8: many_task<8>(w, u, lane, stage); break;
+        case 9: many_task<9>(w, u, lane, stage); break;
+        case 10: many_task<10>(w, u, lane, stage); break;
+        case 11: many_task<11>(w, u, lane, stage); break;
+        case 12: many_task<12>(w, u, lane, stage); break;
+        case 13: many_task<13>(w, u, lane, stage); break;
+        case 14: many_task<14>(w, u, lane, stage); break;
+        case 15: many_task<15>(w, u, lane, stage); break;
+        default: many_task<16>(w, u, lane, stage); break;
         }
     }
 }
@@ -242,7 +246,8 @@ hlf_status hlf_enumerate_store_many(hlf_many* m, hlf_handle* const* hs, const ui
     const uint64_t warps_cap = (uint64_t)hlf::sm_count() * 2 * (hlf::kThreads / 32);
     const uint64_t warps = tasks < warps_cap ? tasks : warps_cap;
     const unsigned blocks = (unsigned)((warps * 32 + hlf::kThreads - 1) / hlf::kThreads);
-    hlf::many_kernel<<<blocks, hlf::kThreads, 0, s>>>(m->dev[b], used, tasks);
+    constexpr size_t smem = (size_t)(hlf::kThreads / 32) * hlf::stage_words<HLF_MAX_W>() * sizeof(uint64_t);
+    hlf::many_kernel<<<blocks, hlf::kThreads, smem, s>>>(m->dev[b], used, tasks);
     if (cudaGetLastError() != cudaSuccess) return HLF_ERR_CUDA;
     if (cudaEventRecord(m->done[b], s) != cudaSuccess) return HLF_ERR_CUDA;
     // every handle read by this launch must outlive it (hlf_destroy waits)

@@ -55,7 +55,11 @@ KERNEL_SOURCES = {
     "store_kernel<1,2>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
     "dense1_kernel<16,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
-TRAFFIC = {}  # kernel -> {"bytes": per-launch DRAM bytes, "sources": digest}
+TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
+    "reduce_kernel<1,4>": {"bytes": 749312 + 0, "sources": "4b0221c93ed21268"},
+    "store_kernel<1,2>": {"bytes": 130048 + 8524999680, "sources": "4b0221c93ed21268"},
+    "dense1_kernel<16,1>": {"bytes": 147456 + 4767026944, "sources": "692c56301d53c78c"},
+}
 
 
 def source_digest(kernel: str) -> str:

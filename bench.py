@@ -51,12 +51,12 @@ SAMPLE_SEED = 99
 # once those sources change, the figure no longer describes the kernel and
 # the line reports null.
 KERNEL_SOURCES = {
-    "reduce_kernel<1,4>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
+    "reduce_kernel<1,6,1024>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
     "store_kernel<1,2>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
     "dense1_kernel<16,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
-    "reduce_kernel<1,4>": {"bytes": 749312 + 0, "sources": "4b0221c93ed21268"},
+    "reduce_kernel<1,6,1024>": {"bytes": 749312 + 0, "sources": "4b0221c93ed21268"},
     "store_kernel<1,2>": {"bytes": 130048 + 8524999680, "sources": "4b0221c93ed21268"},
     "dense1_kernel<16,1>": {"bytes": 147456 + 4767026944, "sources": "692c56301d53c78c"},
 }
@@ -352,8 +352,8 @@ def run_hlf(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(r, total, store_n),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                         "frac": achieved / alu_peak, "traffic": traffic("reduce_kernel<1,4>"),
-                         "kernel": "reduce_kernel<1,4>",
+                         "frac": achieved / alu_peak, "traffic": traffic("reduce_kernel<1,6,1024>"),
+                         "kernel": "reduce_kernel<1,6,1024>",
                          "ms_per_launch": reduce_ms,
                          "peak_basis": f"{sms} SMs x {ISSUE_LANES_PER_SM_CLK} int32 lanes/clk x "
                                        f"{pk['sm_max_mhz']:.0f} MHz (issue limit)",

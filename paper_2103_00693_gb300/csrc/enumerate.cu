@@ -36,10 +36,11 @@ namespace {
 
 
 
-template <int W, int U>
-__global__ void __launch_bounds__(kThreads, min_ctas_for(W)) reduce_kernel(const uint64_t* __restrict__ table, uint64_t offset,
-                                                          uint64_t count, uint64_t per_thread,
-                                                          uint64_t threads_used, hlf_reduce* __restrict__ out)
+template <int W, int U, int T>
+__global__ void __launch_bounds__(T, min_ctas_for(W)) reduce_kernel(const uint64_t* __restrict__ table,
+                                                                   uint64_t offset, uint64_t count,
+                                                                   uint64_t per_thread, uint64_t threads_used,
+                                                                   hlf_reduce* __restrict__ out)
 {
     __shared__ Table<W> t;
     load_table_hash_domain<W>(t, table);
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas_for(W)) reduce_kernel(const
             reduce_run<W, U>(t, offset + a, len, acc);
         }
     }
-    block_reduce<W>(cnt, acc);
+    block_reduce<W, T>(cnt, acc);
     if (threadIdx.x == 0 && cnt) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&out->count), (unsigned long long)cnt);
         atomicAdd(reinterpret_cast<unsigned long long*>(&out->hsum), (unsigned long long)acc.hs);
@@ -210,15 +211,16 @@ hlf_status launch_reduce_w(const uint64_t* table, uint64_t offset, uint64_t coun
                            cudaStream_t s)
 {
     constexpr int U = unroll_for(W);
+    constexpr int T = reduce_threads(W);
     // one wave: as many CTAs as fit on every SM at once
     static int fit[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && fit[dev] == 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit[dev], reduce_kernel<W, U>, kThreads, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit[dev], reduce_kernel<W, U, T>, T, 0) != cudaSuccess)
         return HLF_ERR_CUDA;
     const int per_sm = (dev < 64 && fit[dev] > 0) ? fit[dev] : 1;
-    const uint64_t max_threads = (uint64_t)sm_count() * per_sm * kThreads;
+    const uint64_t max_threads = (uint64_t)sm_count() * per_sm * T;
     const uint64_t min_run = 2048;  // amortises the <= 64-row seed
     uint64_t threads = (count + min_run - 1) / min_run;
     if (threads > max_threads) threads = max_threads;
@@ -226,8 +228,8 @@ hlf_status launch_reduce_w(const uint64_t* table, uint64_t offset, uint64_t coun
     uint64_t per_thread = (count + threads - 1) / threads;
     per_thread = (per_thread + (1ull << U) - 1) & ~((1ull << U) - 1);  // keep runs aligned
     const uint64_t used = (count + per_thread - 1) / per_thread;
-    const unsigned blocks = (unsigned)((used + kThreads - 1) / kThreads);
-    reduce_kernel<W, U><<<blocks, kThreads, 0, s>>>(table, offset, count, per_thread, used, out);
+    const unsigned blocks = (unsigned)((used + T - 1) / T);
+    reduce_kernel<W, U, T><<<blocks, T, 0, s>>>(table, offset, count, per_thread, used, out);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 

@@ -81,11 +81,13 @@ __device__ void batch_factor(const BatchArgs& a, int b, int n, unsigned char* sm
 template <int W>
 __device__ void batch_chunk(const BatchArgs& a, int b, uint64_t first, uint64_t len, unsigned char* smem)
 {
-    constexpr int U = unroll_for(W);
+    constexpr int U = reduce_unroll(W);
+    constexpr uint64_t kBlk = 1ull << U;
     Table<W>& t = *reinterpret_cast<Table<W>*>(smem);
     load_table_hash_domain<W>(t, a.tables + (size_t)b * kTableSlot);
     __syncthreads();
-    const uint64_t per = ((len + blockDim.x - 1) / blockDim.x + 15) & ~15ull;
+    // per-thread runs of whole 2^U blocks (chunks start at multiples of 2^U)
+    const uint64_t per = ((len + blockDim.x - 1) / blockDim.x + kBlk - 1) & ~(kBlk - 1);
     Acc<W> acc;
     acc.zero();
     uint64_t cnt = 0;

@@ -210,7 +210,7 @@ template <int W>
 hlf_status launch_reduce_w(const uint64_t* table, uint64_t offset, uint64_t count, hlf_reduce* out,
                            cudaStream_t s)
 {
-    constexpr int U = unroll_for(W);
+    constexpr int U = reduce_unroll(W);
     constexpr int T = reduce_threads(W);
     // one wave: as many CTAs as fit on every SM at once
     static int fit[64] = {0};

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 CTAS_PER_SM = (1, 2, 3, 0)          # 0 = as many as fit
-CHUNKS = (1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17)
+CHUNKS = (1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)
 CACHE = os.path.join(_build.OUT_DIR, "autotune.json")
 
 

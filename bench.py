@@ -56,9 +56,9 @@ KERNEL_SOURCES = {
     "dense1_kernel<16,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
-    "reduce_kernel<1,6,1024>": {"bytes": 749312 + 0, "sources": "4b0221c93ed21268"},
-    "store_kernel<1,2>": {"bytes": 130048 + 8524999680, "sources": "4b0221c93ed21268"},
-    "dense1_kernel<16,1>": {"bytes": 147456 + 4767026944, "sources": "692c56301d53c78c"},
+    "reduce_kernel<1,6,1024>": {"bytes": 530688 + 0, "sources": "b223622568dda4d7"},
+    "store_kernel<1,2>": {"bytes": 315904 + 8525039360, "sources": "b223622568dda4d7"},
+    "dense1_kernel<16,1>": {"bytes": 164096 + 4767172864, "sources": "3cd4a3044912f731"},
 }
 
 

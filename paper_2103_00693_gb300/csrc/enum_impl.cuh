@@ -16,13 +16,13 @@ constexpr int kThreads = 256;
 // cycles; beyond W = 1 each solution is already 24W - 4 operations, and
 // deeper unrolling only costs registers (occupancy).
 constexpr int unroll_for(int W) { return W == 1 ? 6 : (W == 2 ? 2 : 1); }
-// Shape of the single-instance reduce: at W <= 2 one CTA of 1024 threads per
-// SM with 64 registers each and a deeper unroll (2^6 solutions per block at
-// W = 1, 2^4 at W = 2): measured 7-9% faster than several 256-thread CTAs
-// with 40-44 registers each.
-constexpr int reduce_unroll(int W) { return W == 1 ? 6 : (W == 2 ? 4 : 1); }
-constexpr int reduce_threads(int W) { return W <= 2 ? 1024 : kThreads; }
-constexpr int min_ctas_for(int W) { return W <= 2 ? 1 : (W <= 4 ? 4 : 2); }
+// Shape of the single-instance reduce: at W <= 4 one CTA of 1024 threads per
+// SM with up to 64 registers each and a deeper unroll (2^6 solutions per
+// block at W = 1, 2^4 at W = 2, 2^2 at W = 3, 4): measured 7-10% faster than
+// several 256-thread CTAs with 40-44 registers each.
+constexpr int reduce_unroll(int W) { return W == 1 ? 6 : (W == 2 ? 4 : (W <= 4 ? 2 : 1)); }
+constexpr int reduce_threads(int W) { return W <= 4 ? 1024 : kThreads; }
+constexpr int min_ctas_for(int W) { return W <= 4 ? 1 : 2; }
 
 template <int W>
 struct Table {

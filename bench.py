@@ -53,12 +53,12 @@ SAMPLE_SEED = 99
 KERNEL_SOURCES = {
     "reduce_kernel<1,6,1024>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
     "store_kernel<1,2>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
-    "dense1_kernel<16,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
+    "dense1_kernel<16,1,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
     "reduce_kernel<1,6,1024>": {"bytes": 530688 + 0, "sources": "b223622568dda4d7"},
     "store_kernel<1,2>": {"bytes": 315904 + 8525039360, "sources": "b223622568dda4d7"},
-    "dense1_kernel<16,1>": {"bytes": 164096 + 4767172864, "sources": "3cd4a3044912f731"},
+    "dense1_kernel<16,1,1>": {"bytes": 164096 + 4767172864, "sources": "3cd4a3044912f731"},
 }
 
 
@@ -413,8 +413,8 @@ def run_next_rows(args, A_dev, n, W, store_n, pk, dev):
                             "roofline": {"bound": "hbm", "achieved": dbytes / (d_ms / 1e3) / 1e9,
                                          "peak": pk["hbm_gbs"], "unit": "GB/s",
                                          "frac": dbytes / (d_ms / 1e3) / 1e9 / pk["hbm_gbs"],
-                                         "kernel": "dense1_kernel<16,1>",
-                                         "traffic": traffic("dense1_kernel<16,1>")}},
+                                         "kernel": "dense1_kernel<16,1,1>",
+                                         "traffic": traffic("dense1_kernel<16,1,1>")}},
             "histogram": {"solutions": hcount, "field": "bits 0..13", "ms_per_launch": h_ms,
                           "solutions_per_s": hcount / (h_ms / 1e3)}}
 

@@ -9,8 +9,9 @@
 // boundary and solution t of a run sits at bit (t*n) mod 64 of its word in
 // every lane alike, so the lanes append their solutions to a two-word bit
 // buffer in lockstep and stage each completed word in shared memory; after 32
-// runs (one per lane, a "pass") the warp copies the pass's 32*M*n/64 words
-// out, coalesced. Inside a run, solution t+1 is solution t XOR B_ctz(i+1);
+// runs (one per lane, a "pass") the pass's 32*M*n/64 words leave in one TMA
+// bulk store (cp.async.bulk, double-buffered staging) when the output is
+// 16-byte aligned, else the warp copies them out, coalesced. Inside a run, solution t+1 is solution t XOR B_ctz(i+1);
 // that row index depends only on i mod M except at the one step of a run
 // where i+1 is a multiple of M, so every other step uses a row shared by all
 // lanes (compile-time registers when the window offset is a multiple of M, a
@@ -148,6 +149,7 @@ struct Dense1Plan {
     uint64_t per_warp;  // consecutive passes per warp
     uint64_t words;     // ceil(count * n / 64), the stream's length in words
     int n, wpr;         // wpr = M * n / 64 words per run
+    int nbuf;           // staging buffers per warp (2: a pass overlaps the bulk store of the last)
 };
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
@@ -221,13 +223,40 @@ __device__ __forceinline__ void dense1_run(uint64_t z, uint64_t i0, uint64_t val
     Dense1Step<M, 0, Aligned, Tail>::go(z, lo, fill, w, valid, (uint32_t)n, s_step, Breg, tstar, sp, mine);
 }
 
-template <int M, bool Aligned>
+// Bulk (TMA) stores from shared to global memory: a whole pass's words leave
+// in one cp.async.bulk issued by lane 0, tracked in bulk groups of that lane.
+// Source and destination are 16-byte aligned and the size is a multiple of
+// 16 bytes (checked by the launcher).
+__device__ __forceinline__ void fence_smem_to_async_proxy()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store(uint64_t* gdst, const uint64_t* ssrc, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()  // at most N groups still reading shared memory
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all()
+{
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Bulk: the output is 16-byte aligned, so full passes leave as bulk stores;
+// otherwise (and for the last, partial pass) the warp copies its words out.
+template <int M, bool Aligned, bool Bulk>
 __global__ void __launch_bounds__(kD1Threads, M == 64 ? 3 : 4) dense1_kernel(const uint64_t* __restrict__ table, Dense1Plan pl,
                                                             uint64_t* __restrict__ out)
 {
     constexpr int A = ilog2(M);
     constexpr int b = A + 5;  // a pass advances every run start by 32 M = 2^b
-    extern __shared__ __align__(16) uint64_t s_stage[];  // [warps][32 * wpr]
+    extern __shared__ __align__(16) uint64_t s_stage[];  // [warps][nbuf][32 * wpr]
     __shared__ uint64_t s_B[kTableRows];
     __shared__ uint64_t s_step[M];
     __shared__ uint64_t s_z0;
@@ -255,8 +284,7 @@ __global__ void __launch_bounds__(kD1Threads, M == 64 ? 3 : 4) dense1_kernel(con
     const uint64_t P1 = min(P0 + pl.per_warp, pl.passes);
     const int n = pl.n;
     const uint64_t pass_words = 32ull * (uint64_t)pl.wpr;
-    uint64_t* stage = s_stage + (size_t)warp * pass_words;
-    uint64_t* mine = stage + (size_t)lane * pl.wpr;
+    uint64_t* const stages = s_stage + (size_t)warp * pl.nbuf * pass_words;
 
     uint64_t j0 = (P0 * 32 + (uint64_t)lane) * M;  // run start, relative to the window
     uint64_t i0 = pl.offset + j0;                  // and absolute
@@ -264,28 +292,44 @@ __global__ void __launch_bounds__(kD1Threads, M == 64 ? 3 : 4) dense1_kernel(con
     for (uint64_t g = i0 ^ (i0 >> 1); g; g &= g - 1) zs ^= s_B[__ffsll((long long)g) - 1];
 
     for (uint64_t P = P0;;) {
+        uint64_t* stage = stages + (size_t)((P - P0) & (uint64_t)(pl.nbuf - 1)) * pass_words;
+        uint64_t* mine = stage + (size_t)lane * pl.wpr;
+        if constexpr (Bulk) {  // the bulk store that last read this buffer is done reading it
+            if (lane == 0) {
+                if (pl.nbuf == 2) bulk_wait_read<1>();
+                else bulk_wait_read<0>();
+            }
+            __syncwarp();
+        }
         if (P < pl.full) {
             dense1_run<M, Aligned, false>(zs, i0, M, n, s_B, s_step, Breg, tstar, mine);
         } else {
             const uint64_t valid = j0 < pl.count ? min(pl.count - j0, (uint64_t)M) : 0;
             dense1_run<M, Aligned, true>(zs, i0, valid, n, s_B, s_step, Breg, tstar, mine);
         }
-        __syncwarp();
         const uint64_t w0 = P * pass_words;
         const int nw = (int)min(pass_words, pl.words - w0);
-        for (int q = lane; q < nw; q += 32) st_cs(out + w0 + q, stage[q]);
-        __syncwarp();
+        if (Bulk && nw == (int)pass_words) {
+            fence_smem_to_async_proxy();  // this lane's staged words, before the async proxy reads them
+            __syncwarp();
+            if (lane == 0) bulk_store(out + w0, stage, (uint32_t)(pass_words * sizeof(uint64_t)));
+        } else {
+            __syncwarp();
+            for (int q = lane; q < nw; q += 32) st_cs(out + w0 + q, stage[q]);
+            __syncwarp();
+        }
         if (++P == P1) break;
         const int c = b + ctz64(~(i0 >> b));  // <= 64: the top b bits of i0 >> b are 0
         zs ^= s_B[b - 1] ^ s_B[c];
         i0 += 32ull * M;
         j0 += 32ull * M;
     }
+    if (Bulk && lane == 0) bulk_wait_all();  // shared memory stays valid until the stores are done
 }
 
-template <int M, bool Aligned>
-hlf_status launch_dense1(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
-                         cudaStream_t s)
+template <int M, bool Aligned, bool Bulk>
+hlf_status launch_dense1_k(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
+                           cudaStream_t s)
 {
     constexpr uint64_t per_pass = 32ull * M;
     Dense1Plan pl{};
@@ -296,19 +340,21 @@ hlf_status launch_dense1(const uint64_t* table, int n, uint64_t offset, uint64_t
     pl.full = count / per_pass;
     pl.passes = pl.full + (count % per_pass != 0);
     pl.words = (count * (uint64_t)n + 63) / 64;  // count * n <= 2^64 - 64 (checked by the caller)
-    const size_t smem = (size_t)kD1Warps * 32 * pl.wpr * sizeof(uint64_t);
+    // two buffers per warp while a CTA's staging stays within 64 KB (wpr <= 16)
+    pl.nbuf = (Bulk && pl.wpr <= 16) ? 2 : 1;
+    const size_t smem = (size_t)kD1Warps * pl.nbuf * 32 * pl.wpr * sizeof(uint64_t);
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
-        const int most = kD1Warps * 32 * (M * 63 / 64) * (int)sizeof(uint64_t);  // n <= 63
-        if (cudaFuncSetAttribute(dense1_kernel<M, Aligned>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
-            cudaSuccess)
+        const int most = kD1Warps * 32 * 64 * (int)sizeof(uint64_t);  // 128 KB: wpr <= 63 with one buffer
+        if (cudaFuncSetAttribute(dense1_kernel<M, Aligned, Bulk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 most) != cudaSuccess)
             return HLF_ERR_CUDA;
         attr_set[dev] = true;
     }
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense1_kernel<M, Aligned>, kD1Threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense1_kernel<M, Aligned, Bulk>, kD1Threads, smem) !=
         cudaSuccess)
         return HLF_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
@@ -317,8 +363,17 @@ hlf_status launch_dense1(const uint64_t* table, int n, uint64_t offset, uint64_t
     pl.per_warp = (pl.passes + warps - 1) / warps;
     const uint64_t used = (pl.passes + pl.per_warp - 1) / pl.per_warp;
     const unsigned blocks = (unsigned)((used + kD1Warps - 1) / kD1Warps);
-    dense1_kernel<M, Aligned><<<blocks, kD1Threads, smem, s>>>(table, pl, out);
+    dense1_kernel<M, Aligned, Bulk><<<blocks, kD1Threads, smem, s>>>(table, pl, out);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+}
+
+template <int M, bool Aligned>
+hlf_status launch_dense1(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
+                         cudaStream_t s)
+{
+    // a pass is 256 * wpr bytes, so pass starts are 16-byte aligned when out is
+    if (reinterpret_cast<uintptr_t>(out) % 16 == 0) return launch_dense1_k<M, Aligned, true>(table, n, offset, count, out, s);
+    return launch_dense1_k<M, Aligned, false>(table, n, offset, count, out, s);
 }
 
 // ------------------------------------------------------------ n >= 64

@@ -79,8 +79,9 @@ def test_dense_one_word_rows(cuda_ok, n):
     """n <= 64, every n: lane runs of M = max(64 / gcd(n, 64), 16) solutions
     (16, 32 or 64), window offsets that are and are not multiples of M, a
     single solution, ragged last passes, and windows long enough that each
-    warp walks several passes. For n = 64, an output that is 16-byte aligned
-    (the packed store) and one that is only 8-byte aligned."""
+    warp walks several passes. Outputs that are 16-byte aligned (full passes
+    leave as bulk stores; at n = 64 the packed store runs) and outputs that
+    are only 8-byte aligned (the warp copies every pass out itself)."""
     import torch
 
     A = synth.random_symmetric(n, 0.3, 100 + n)
@@ -94,7 +95,7 @@ def test_dense_one_word_rows(cuda_ok, n):
             off = off & ~63 if aligned else off | 1
             off = min(off, space - cnt)
             words = hlf.dense_words(cnt, n)
-            for lead in ((0, 1) if n == 64 else (0,)):
+            for lead in (0, 1):
                 buf = torch.full((words + 3,), -1, dtype=torch.int64, device="cuda")
                 G.store_dense(off, cnt, buf[lead:])
                 got = buf.cpu().numpy().view(np.uint64)

@@ -3,140 +3,34 @@
 // instead of W whole words. For n = 36 that is 36 bits instead of 64 per
 // solution. The solutions are those of hlf_enumerate_store.
 //
-// n < 64 (one word per row), dense1_kernel: a lane owns a run of M
+// n < 64, dense1_kernel: a lane owns a run of M
 // consecutive solutions whose bits fill whole words, M*n being a multiple of
 // 64 (M = max(64 / gcd(n, 64), 16)). Every run therefore starts on a word
 // boundary and solution t of a run sits at bit (t*n) mod 64 of its word in
 // every lane alike, so the lanes append their solutions to a two-word bit
-// buffer in lockstep and stage each completed word in shared memory; after 32
-// runs (one per lane, a "pass") the pass's 32*M*n/64 words leave in one TMA
-// bulk store (cp.async.bulk, double-buffered staging) when the output is
-// 16-byte aligned, else the warp copies them out, coalesced. Inside a run, solution t+1 is solution t XOR B_ctz(i+1);
-// that row index depends only on i mod M except at the one step of a run
-// where i+1 is a multiple of M, so every other step uses a row shared by all
-// lanes (compile-time registers when the window offset is a multiple of M, a
-// shared-memory table otherwise). From one pass to the next a lane's run
-// start x advances by 32*M = 2^b, and g(x) ^ g(x + 2^b) has exactly bits b-1
-// and c, c = b + (number of trailing ones of x >> b): two row XORs.
+// buffer in lockstep and stage each completed word in shared memory. After
+// 32 runs (one per lane, a "pass") the pass's 32*M*n/64 words leave in one
+// TMA bulk store (cp.async.bulk, double-buffered staging) when the output is
+// 16-byte aligned; otherwise the warp copies them out, coalesced. Inside a
+// run, solution t+1 is solution t XOR B_ctz(i+1); that row index depends
+// only on i mod M except at the one step of a run where i+1 is a multiple of
+// M, so every other step uses a row shared by all lanes (compile-time
+// registers when the window offset is a multiple of M, a shared-memory table
+// otherwise). From one pass to the next a lane's run start x advances by
+// 32*M = 2^b, and g(x) ^ g(x + 2^b) has exactly bits b-1 and c,
+// c = b + (number of trailing ones of x >> b): two row XORs.
 //
-// n = 64 with a 16-byte aligned output is the packed store itself; otherwise
-// (n >= 64), dense_kernel: a warp produces 64
-// consecutive solutions per step; 64 solutions of n bits are exactly n words,
-// so every group's words start on a word boundary for any n. Each lane walks
-// two Gray chains (relative positions 2*lane and 2*lane+1 of the group) that
-// advance by 64 in absolute index per step: with i = 64 H + l,
-// z(i + 64) = z(i) ^ B_5 ^ B_{6 + ctz(H + 1)} (the lane-interleaved identity
-// of enumerate.cu), so a step is one row XOR per solution whatever the
-// window's offset. The group's 64 solutions are staged in shared memory;
-// output word j of a group holds stream bits [64 j, 64 j + 64), which start
-// at bit o of solution s, with (s, o) taken from a per-CTA table built once
-// (no division in the loop). Each lane assembles whole output words with
-// shifts, and the warp writes the group's n words out, coalesced.
+// n = 64 is the packed store itself (hlf_enumerate_store's kernel, which also
+// takes the 8-byte aligned outputs this entry point allows).
+//
+// n > 64, dense2_kernel: 64 solutions of n bits are exactly n words, so a
+// warp produces one such group per step, two solutions per lane, each placed
+// with funnel shifts at its bit offset in the group (see dense2_kernel).
 
 #include "enum_impl.cuh"
 
 namespace hlf {
 namespace {
-
-constexpr int kDenseGroup = 64;
-constexpr int kDenseSteps = kTableRows - 6;  // C_j = B_5 ^ B_{6+j}, j = 0..58
-
-struct DensePlan {
-    uint64_t offset, count;
-    uint64_t groups;    // ceil(count / 64)
-    uint64_t per_warp;  // groups per warp
-    int n;
-};
-
-// `len` (1..64) bits of a W-word solution starting at bit `pos`.
-template <int W>
-__device__ __forceinline__ uint64_t extract_bits(const uint64_t* sol, int pos, int len)
-{
-    const int w = pos >> 6;
-    const int sh = pos & 63;
-    uint64_t v = sol[w] >> sh;
-    if (sh && sh + len > 64) v |= sol[w + 1] << (64 - sh);
-    return len == 64 ? v : v & ((1ull << len) - 1);
-}
-
-template <int W>
-__global__ void __launch_bounds__(kThreads) dense_kernel(const uint64_t* __restrict__ table, DensePlan pl,
-                                                         uint64_t* __restrict__ out)
-{
-    extern __shared__ __align__(16) uint64_t s_dyn[];
-    // [n] start words (s << 16 | o: output word j starts at bit o of solution s), then [warps][64][W] solutions
-    uint32_t* s_start = reinterpret_cast<uint32_t*>(s_dyn);
-    __shared__ Table<W> t;
-    __shared__ uint64_t s_C[kDenseSteps][W];
-    const int n = pl.n;
-    uint64_t* s_sol = s_dyn + (n + 1) / 2;
-    load_table<W>(t, table);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kDenseSteps * W; i += blockDim.x) {
-        const int j = i / W, w = i % W;
-        s_C[j][w] = t.B[5][w] ^ t.B[6 + j][w];
-    }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int s = (64 * j) / n;
-        s_start[j] = ((uint32_t)s << 16) | (uint32_t)(64 * j - s * n);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    uint64_t* sol = s_sol + (size_t)warp * kDenseGroup * W;
-    const uint64_t wg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t k0 = wg * pl.per_warp;
-    if (k0 >= pl.groups) return;
-    const uint64_t k1 = min(k0 + pl.per_warp, pl.groups);
-
-    uint64_t z[2][W];
-    uint64_t H[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const uint64_t i = pl.offset + (uint64_t)kDenseGroup * k0 + (uint64_t)(2 * lane + e);
-        H[e] = i >> 6;
-        seed<W>(t, i, z[e]);
-    }
-    for (uint64_t k = k0;;) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e)
-#pragma unroll
-            for (int w = 0; w < W; ++w) sol[(2 * lane + e) * W + w] = z[e][w];
-        __syncwarp();
-        const uint64_t rem = pl.count - (uint64_t)kDenseGroup * k;
-        const int valid = rem < kDenseGroup ? (int)rem : kDenseGroup;
-        uint64_t* dst = out + k * (uint64_t)n;
-        const int nwords = (valid * n + 63) >> 6;
-        for (int j = lane; j < nwords; j += 32) {
-            const uint32_t st = s_start[j];
-            int s = (int)(st >> 16);
-            const int o = (int)(st & 0xffff);
-            uint64_t v;
-            int got;
-            if constexpr (W == 1) {
-                v = sol[s] >> o;
-                got = n - o;
-                for (++s; got < 64 && s < valid; ++s, got += n) v |= sol[s] << got;
-            } else {
-                got = min(64, n - o);
-                v = extract_bits<W>(sol + s * W, o, got);
-                for (++s; got < 64 && s < valid; ++s) {
-                    const int take = min(n, 64 - got);
-                    v |= extract_bits<W>(sol + s * W, 0, take) << got;
-                    got += take;
-                }
-            }
-            dst[j] = v;
-        }
-        __syncwarp();
-        if (++k == k1) break;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            H[e] += 1;
-            xor_row<W>(z[e], s_C[ctz64(H[e])]);
-        }
-    }
-}
 
 // ------------------------------------------------------------ n < 64
 constexpr int kD1Threads = 256;
@@ -376,42 +270,170 @@ hlf_status launch_dense1(const uint64_t* table, int n, uint64_t offset, uint64_t
     return launch_dense1_k<M, Aligned, false>(table, n, offset, count, out, s);
 }
 
-// ------------------------------------------------------------ n >= 64
-template <int W>
-hlf_status launch_dense_w(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
-                          cudaStream_t s)
+// ------------------------------------------------------------ n > 64
+constexpr int kD2Threads = 256;
+constexpr int kD2Warps = kD2Threads / 32;
+constexpr int kD2Steps = kTableRows - 6;  // C_j = B_5 ^ B_{6+j}, j = 0..58
+
+struct Dense2Plan {
+    uint64_t offset, count;
+    uint64_t groups;    // ceil(count / 64); a group is 64 solutions, n words of the stream
+    uint64_t full;      // groups with all 64 solutions inside the window
+    uint64_t per_warp;  // consecutive groups per warp
+    uint64_t words;     // ceil(count * n / 64)
+    int n, nbuf;        // nbuf: staging buffers of n words per warp
+};
+
+// Solution z (W words, n > 64 bits) placed at bit c of st[0]: the words
+// st[0..L], L = (c + n - 1) / 64, each written plainly, or merged (read, OR,
+// write) where the first or last word is shared with a neighbour already
+// placed. Tail: an invalid solution places zeros.
+template <int W, bool Tail>
+__device__ __forceinline__ void dense2_put(uint64_t* st, const uint64_t (&z)[W], bool valid, uint32_t c, int L,
+                                           bool merge_first, bool merge_last)
 {
-    DensePlan pl{};
+    uint64_t prev = 0;
+#pragma unroll
+    for (int w = 0; w <= W; ++w) {
+        const uint64_t cur = (w < W && (!Tail || valid)) ? z[w] : 0ull;
+        const uint64_t v = shl64(cur, c) | shr64(prev, 64 - c);
+        prev = cur;
+        if (w <= L) {
+            if ((w == 0 && merge_first) || (w == L && merge_last)) st[w] |= v;
+            else st[w] = v;
+        }
+    }
+}
+
+// A warp produces one group (64 solutions, exactly n words) per step. Lane l
+// walks the solutions 2l and 2l+1 of each group, which advance by 64 in
+// absolute index per step: with i = 64 H + t, z(i + 64) = z(i) ^ B_5 ^
+// B_{6 + ctz(H + 1)} (the lane-interleaved identity of enumerate.cu). Solution
+// t starts at bit t*n of the group, word (t*n) / 64, bit (t*n) % 64, and fills
+// W or W+1 words. As n > 64, a word holds bits of at most two solutions, and
+// solutions t and t+2 share none: the even solutions place their words first,
+// plainly, then the odd ones merge into the first and last words they share.
+// The group's words leave in one bulk store when the output is 16-byte aligned
+// and n is even (n*8 bytes, a multiple of 16), else the warp copies them out.
+template <int W, bool Bulk>
+__global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __restrict__ table, Dense2Plan pl,
+                                                            uint64_t* __restrict__ out)
+{
+    extern __shared__ __align__(16) uint64_t s_stage2[];  // [warps][nbuf][n]
+    __shared__ Table<W> t;
+    __shared__ uint64_t s_C[kD2Steps][W];
+    load_table<W>(t, table);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kD2Steps * W; i += blockDim.x) {
+        const int j = i / W, w = i % W;
+        s_C[j][w] = t.B[5][w] ^ t.B[6 + j][w];
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t gw = (uint64_t)blockIdx.x * kD2Warps + warp;
+    const uint64_t k0 = gw * pl.per_warp;
+    if (k0 >= pl.groups) return;
+    const uint64_t k1 = min(k0 + pl.per_warp, pl.groups);
+    const int n = pl.n;
+    uint64_t* const stages = s_stage2 + (size_t)warp * pl.nbuf * n;
+
+    const uint32_t tA = 2 * lane, tB = 2 * lane + 1;  // this lane's solutions in every group
+    const int bA = (int)((tA * n) >> 6), bB = (int)((tB * n) >> 6);
+    const uint32_t cA = (tA * n) & 63, cB = (tB * n) & 63;
+    const int LA = (int)((cA + n - 1) >> 6), LB = (int)((cB + n - 1) >> 6);
+    const bool mfB = cB != 0;                       // B shares its first word with A
+    const bool mlB = (((tB + 1) * n) & 63) != 0;    // and its last with the next lane's A
+
+    uint64_t zA[W], zB[W];
+    const uint64_t iA = pl.offset + 64 * k0 + tA;
+    uint64_t HA = iA >> 6, HB = (iA + 1) >> 6;
+    seed<W>(t, iA, zA);
+    seed<W>(t, iA + 1, zB);
+
+    for (uint64_t k = k0;;) {
+        uint64_t* st = stages + (size_t)((k - k0) & (uint64_t)(pl.nbuf - 1)) * n;
+        if constexpr (Bulk) {  // the bulk store that last read this buffer is done reading it
+            if (lane == 0) {
+                if (pl.nbuf == 2) bulk_wait_read<1>();
+                else bulk_wait_read<0>();
+            }
+            __syncwarp();
+        }
+        if (k < pl.full) {
+            dense2_put<W, false>(st + bA, zA, true, cA, LA, false, false);
+            __syncwarp();
+            dense2_put<W, false>(st + bB, zB, true, cB, LB, mfB, mlB);
+        } else {
+            const uint64_t rem = pl.count - 64 * k;
+            dense2_put<W, true>(st + bA, zA, tA < rem, cA, LA, false, false);
+            __syncwarp();
+            dense2_put<W, true>(st + bB, zB, tB < rem, cB, LB, mfB, mlB);
+        }
+        const uint64_t w0 = k * (uint64_t)n;
+        const int nw = (int)min((uint64_t)n, pl.words - w0);
+        if (Bulk && nw == n) {
+            fence_smem_to_async_proxy();
+            __syncwarp();
+            if (lane == 0) bulk_store(out + w0, st, (uint32_t)(n * sizeof(uint64_t)));
+        } else {
+            __syncwarp();
+            for (int q = lane; q < nw; q += 32) st_cs(out + w0 + q, st[q]);
+            __syncwarp();
+        }
+        if (++k == k1) break;
+        HA += 1;  // H < 2^58, so ctz(H + 1) <= 58
+        xor_row<W>(zA, s_C[ctz64(HA)]);
+        HB += 1;
+        xor_row<W>(zB, s_C[ctz64(HB)]);
+    }
+    if (Bulk && lane == 0) bulk_wait_all();
+}
+
+template <int W, bool Bulk>
+hlf_status launch_dense2_k(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
+                           cudaStream_t s)
+{
+    Dense2Plan pl{};
     pl.offset = offset;
     pl.count = count;
     pl.n = n;
-    pl.groups = (count + kDenseGroup - 1) / kDenseGroup;
-    // start table (n x 4 bytes, rounded to words) + 64 solutions of W words per warp
-    const size_t smem = ((size_t)(n + 1) / 2 + (size_t)(kThreads / 32) * kDenseGroup * W) * sizeof(uint64_t);
+    pl.full = count / 64;
+    pl.groups = pl.full + (count % 64 != 0);
+    pl.words = (count * (uint64_t)n + 63) / 64;  // count * n <= 2^64 - 64 (checked by the caller)
+    pl.nbuf = (Bulk && n <= 512) ? 2 : 1;
+    const size_t smem = (size_t)kD2Warps * pl.nbuf * n * sizeof(uint64_t);  // <= 64 KB
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(dense_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((32 * W + (kThreads / 32) * kDenseGroup * W) * sizeof(uint64_t))) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(dense2_kernel<W, Bulk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kD2Warps * 1024 * (int)sizeof(uint64_t)) != cudaSuccess)
             return HLF_ERR_CUDA;
         attr_set[dev] = true;
     }
-    // one wave: as many CTAs as fit on every SM at once (equal work per warp,
-    // so a partial second wave would double the time)
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_kernel<W>, kThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense2_kernel<W, Bulk>, kD2Threads, smem) !=
+        cudaSuccess)
         return HLF_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
-    const uint64_t max_warps = (uint64_t)sm_count() * per_sm * (kThreads / 32);
-    uint64_t warps = (pl.groups + 15) / 16;
-    if (warps > max_warps) warps = max_warps;
-    if (warps == 0) warps = 1;
+    const uint64_t max_warps = (uint64_t)sm_count() * per_sm * kD2Warps;
+    const uint64_t warps = pl.groups < max_warps ? pl.groups : max_warps;
     pl.per_warp = (pl.groups + warps - 1) / warps;
-    const unsigned blocks = (unsigned)((warps * 32 + kThreads - 1) / kThreads);
-    dense_kernel<W><<<blocks, kThreads, smem, s>>>(table, pl, out);
+    const uint64_t used = (pl.groups + pl.per_warp - 1) / pl.per_warp;
+    const unsigned blocks = (unsigned)((used + kD2Warps - 1) / kD2Warps);
+    dense2_kernel<W, Bulk><<<blocks, kD2Threads, smem, s>>>(table, pl, out);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+}
+
+template <int W>
+hlf_status launch_dense2(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
+                         cudaStream_t s)
+{
+    if (reinterpret_cast<uintptr_t>(out) % 16 == 0 && n % 2 == 0)
+        return launch_dense2_k<W, true>(table, n, offset, count, out, s);
+    return launch_dense2_k<W, false>(table, n, offset, count, out, s);
 }
 
 }  // namespace
@@ -419,6 +441,7 @@ hlf_status launch_dense_w(const uint64_t* table, int n, uint64_t offset, uint64_
 hlf_status launch_store_dense(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
                               cudaStream_t s)
 {
+    if (n == 64) return launch_store(table, 1, offset, count, out, s);  // one whole word per solution
     if (n < 64) {
         const int m = 64 / (n & -n);  // 64 / gcd(n, 64)
         const int M = m < 16 ? 16 : m;
@@ -432,25 +455,22 @@ hlf_status launch_store_dense(const uint64_t* table, int n, uint64_t offset, uin
                                 : launch_dense1<64, false>(table, n, offset, count, out, s);
         }
     }
-    if (n == 64 && reinterpret_cast<uintptr_t>(out) % 16 == 0)  // one whole word per solution
-        return launch_store(table, 1, offset, count, out, s);
     switch ((n + 63) / 64) {
-    case 1: return launch_dense_w<1>(table, n, offset, count, out, s);
-    case 2: return launch_dense_w<2>(table, n, offset, count, out, s);
-    case 3: return launch_dense_w<3>(table, n, offset, count, out, s);
-    case 4: return launch_dense_w<4>(table, n, offset, count, out, s);
-    case 5: return launch_dense_w<5>(table, n, offset, count, out, s);
-    case 6: return launch_dense_w<6>(table, n, offset, count, out, s);
-    case 7: return launch_dense_w<7>(table, n, offset, count, out, s);
-    case 8: return launch_dense_w<8>(table, n, offset, count, out, s);
-    case 9: return launch_dense_w<9>(table, n, offset, count, out, s);
-    case 10: return launch_dense_w<10>(table, n, offset, count, out, s);
-    case 11: return launch_dense_w<11>(table, n, offset, count, out, s);
-    case 12: return launch_dense_w<12>(table, n, offset, count, out, s);
-    case 13: return launch_dense_w<13>(table, n, offset, count, out, s);
-    case 14: return launch_dense_w<14>(table, n, offset, count, out, s);
-    case 15: return launch_dense_w<15>(table, n, offset, count, out, s);
-    case 16: return launch_dense_w<16>(table, n, offset, count, out, s);
+    case 2: return launch_dense2<2>(table, n, offset, count, out, s);
+    case 3: return launch_dense2<3>(table, n, offset, count, out, s);
+    case 4: return launch_dense2<4>(table, n, offset, count, out, s);
+    case 5: return launch_dense2<5>(table, n, offset, count, out, s);
+    case 6: return launch_dense2<6>(table, n, offset, count, out, s);
+    case 7: return launch_dense2<7>(table, n, offset, count, out, s);
+    case 8: return launch_dense2<8>(table, n, offset, count, out, s);
+    case 9: return launch_dense2<9>(table, n, offset, count, out, s);
+    case 10: return launch_dense2<10>(table, n, offset, count, out, s);
+    case 11: return launch_dense2<11>(table, n, offset, count, out, s);
+    case 12: return launch_dense2<12>(table, n, offset, count, out, s);
+    case 13: return launch_dense2<13>(table, n, offset, count, out, s);
+    case 14: return launch_dense2<14>(table, n, offset, count, out, s);
+    case 15: return launch_dense2<15>(table, n, offset, count, out, s);
+    case 16: return launch_dense2<16>(table, n, offset, count, out, s);
     default: return HLF_ERR_SIZE;
     }
 }

@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(kThreads) store_kernel(const uint64_t* __restr
     const uint64_t h1 = min(h0 + pl.per_warp, pl.h_end);
     uint64_t z[W];
     seed<W>(t, h0 * G + (uint64_t)(S * lane), z);
-    const bool even = (pl.offset & 1) == 0;
+    // W = 1: a lane's pair starts at word out + (even index - offset); it is
+    // 16-byte aligned when the output's word index and the offset agree in parity
+    const bool even = (((reinterpret_cast<uintptr_t>(out) >> 3) ^ pl.offset) & 1) == 0;
     for (uint64_t h = h0;;) {
         if constexpr (S == 2) {
             uint64_t* p = out + (h * G + (uint64_t)(S * lane) - pl.offset) * W;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) store_kernel(const uint64_t* __restr
                 st_cs(p, z[0]);
                 st_cs(p + 1, z1);
             }
-        } else {  // out is 16-byte aligned (checked by the caller)
+        } else {  // W > 1: out is 16-byte aligned (checked by the callers)
             store_warp_coalesced<W, true>(out + (h * G - pl.offset) * W, z,
                                           s_stage + (threadIdx.x >> 5) * stage_words<W>(), lane);
         }

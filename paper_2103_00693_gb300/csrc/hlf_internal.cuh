@@ -40,6 +40,7 @@ hlf_status launch_reduce(const uint64_t* table, int W, uint64_t offset, uint64_t
                          hlf_reduce* out, cudaStream_t s);
 hlf_status launch_reduce_chunks(const uint64_t* table, int W, uint64_t offset, uint64_t chunk,
                                 uint64_t n_chunks, hlf_reduce* out, cudaStream_t s);
+// out: 8-byte aligned at W = 1, 16-byte aligned at W > 1.
 hlf_status launch_store(const uint64_t* table, int W, uint64_t offset, uint64_t count,
                         uint64_t* out, cudaStream_t s);
 hlf_status launch_store_dense(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,

@@ -45,3 +45,44 @@ def test_histogram_argument_checks(cuda_ok):
         with pytest.raises(hlf.HlfError):
             hlf.hlf_enumerate_histogram(G.h, 0, 4, lo, nb, out)
     G.close()
+
+
+def _first_rows_independent(F, lo, nb, rows):
+    """Whether the field bits [lo, lo + nb) of the enumeration rows 0..4 are
+    linearly independent over GF(2) (the kernel then walks lane-interleaved)."""
+    vecs = [int(sum(int(b) << j for j, b in enumerate(r[lo:lo + nb]))) for r in rows[:5]]
+    if len(vecs) < 5:
+        return False
+    basis = []
+    for v in vecs:
+        for b in basis:
+            v = min(v, v ^ b)
+        if v == 0:
+            return False
+        basis.append(v)
+    return True
+
+
+@pytest.mark.parametrize("order", ["gray", "paper"])
+def test_histogram_both_walks(cuda_ok, order):
+    """Fields whose bits over the first five enumeration rows are independent
+    (the lane-interleaved walk) and fields where they are not (per-thread
+    runs), each against the oracle over windows with ragged ends."""
+    A = synth.grid_instance(7, 0.5, 21)
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    G.set_order(hlf.ORDER_PAPER if order == "paper" else hlf.ORDER_GRAY)
+    if order == "gray":  # the enumeration rows are the basis rows B_k
+        rows = oc.unpack_rows(F.basis_words(), F.n)
+    else:  # row k is T_0 ^ ... ^ T_k, T_l = A's column at the pivot p_{r-1-l}
+        rows = np.cumsum(F.A[F.piv[::-1]].astype(np.int64), axis=0) % 2
+    seen = set()
+    space = 1 << F.space_log2()
+    for lo, nb in ((0, 10), (0, 14), (30, 12), (40, 9), (3, 5)):
+        seen.add(_first_rows_independent(F, lo, nb, rows))
+        for off, cnt in ((0, min(space, 1 << 17)), (12345, 70001)):
+            cnt = min(cnt, space - off)
+            got = G.histogram(off, cnt, lo, nb).cpu().numpy().view(np.uint64)
+            assert np.array_equal(got, oc.histogram(F, off, cnt, lo, nb, order)), (order, lo, nb, off, cnt)
+    assert seen == {True, False}, "both walks should be exercised"
+    G.close()

@@ -272,17 +272,4 @@ __device__ __forceinline__ void store_warp_coalesced(uint64_t* dst, const uint64
     __syncwarp();  // the stage is rewritten by the next call
 }
 
-template <int W>
-__device__ __forceinline__ void store_one(uint64_t* p, const uint64_t (&z)[W])
-{
-    if constexpr (W % 2 == 0) {
-#pragma unroll
-        for (int w = 0; w < W; w += 2) st_cs_v2(p + w, z[w], z[w + 1]);
-    } else {
-#pragma unroll
-        for (int w = 0; w < W; ++w) st_cs(p + w, z[w]);
-    }
-}
-
-
 }  // namespace hlf

@@ -5,11 +5,15 @@
 //       A in registers (W uint64 words each). For each column c, left to
 //       right, the candidates are the rows not yet used as a pivot that have
 //       bit c set; a min over each warp and then over the warps picks the
-//       lowest such row p. Row p
-//       is broadcast through shared memory and every other row with bit c set
-//       XORs it in (rows above and below: Gauss-Jordan, so the result is the
-//       unique reduced row echelon form). Rows are never swapped; the pivot
-//       row of column c is remembered instead. Unused rows end at zero.
+//       lowest such row p. Each warp stages its lowest candidate's words next
+//       to its index, so one barrier per column suffices: after it every
+//       thread knows p and reads row p from its warp's slot, and every other
+//       row with bit c set XORs it in (rows above and below: Gauss-Jordan, so
+//       the result is the unique reduced row echelon form). The slots
+//       alternate with the column's parity, so a slot is rewritten only after
+//       the next column's barrier, when every read of it is done. Rows are
+//       never swapped; the pivot row of column c is remembered instead.
+//       Unused rows end at zero.
 //   (2)-(4) Kernel basis, q and z^a. For a free column f the kernel vector is
 //       x_f = e_f + sum_k B_k[f] e_{p_k}; q(x_f) = sum over i in supp(x_f) of
 //       popcount(A_i & x_f), mod 4, which is x_f^T A x_f mod 4. With z^a
@@ -26,8 +30,8 @@ namespace hlf {
 
 template <int W, int MAXN>
 struct FactorSmem {
-    int first[2][32];
-    uint64_t prow[2][W];
+    int first[2][32];        // per warp: its lowest candidate row for the column (by column parity)
+    uint64_t crow[2][32][W];  // and that row's words
     int pivcol[MAXN];
     uint32_t pivmask[MAXN / 32];
     uint64_t x[32][W];
@@ -129,30 +133,36 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
 #pragma unroll
             for (int j = R - 1; j >= 0; --j)
                 if (tid + j * bs < n && !used[j] && ((row[j][w] >> b) & 1ull)) cand = tid + j * bs;
-            cand = __reduce_min_sync(0xffffffffu, cand);
-            if (lane == 0) sm.first[buf][warp] = cand;
+            const int wmin = __reduce_min_sync(0xffffffffu, cand);
+            if (wmin != kNone && cand == wmin) {  // this lane holds the warp's lowest candidate
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    if (tid + j * bs != wmin) continue;
+#pragma unroll
+                    for (int v = 0; v < W; ++v) sm.crow[buf][warp][v] = row[j][v];
+                }
+            }
+            if (lane == 0) sm.first[buf][warp] = wmin;
             __syncthreads();
             int p = lane < nwarps ? sm.first[buf][lane] : kNone;
             p = __reduce_min_sync(0xffffffffu, p);
             if (p == kNone) continue;  // no pivot in column c (uniform)
+            const uint64_t* prow = sm.crow[buf][(p % bs) >> 5];
             if (tid == p % bs) {
                 const int pj = p / bs;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     if (j != pj) continue;
-#pragma unroll
-                    for (int v = 0; v < W; ++v) sm.prow[buf][v] = row[j][v];
                     used[j] = true;
                     my_k[j] = rank;
                 }
             }
             if (tid == 0) sm.pivcol[rank] = c;
-            __syncthreads();
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 if (tid + j * bs != p && ((row[j][w] >> b) & 1ull)) {
 #pragma unroll
-                    for (int v = 0; v < W; ++v) row[j][v] ^= sm.prow[buf][v];
+                    for (int v = 0; v < W; ++v) row[j][v] ^= prow[v];
                 }
             }
             ++rank;

@@ -56,9 +56,9 @@ KERNEL_SOURCES = {
     "dense1_kernel<16,1,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
-    "reduce_kernel<1,6,1024>": {"bytes": 966400 + 0, "sources": "dee7b0c6d189c663"},
-    "store_kernel<1,2>": {"bytes": 104448 + 8524793344, "sources": "dee7b0c6d189c663"},
-    "dense1_kernel<16,1,1>": {"bytes": 523520 + 4766974976, "sources": "bddaf979d913f6c0"},
+    "reduce_kernel<1,6,1024>": {"bytes": 897280 + 0, "sources": "12d473f308918f62"},
+    "store_kernel<1,2>": {"bytes": 167936 + 8524608768, "sources": "12d473f308918f62"},
+    "dense1_kernel<16,1,1>": {"bytes": 89600 + 4766977024, "sources": "924d50e6b2f3fffd"},
 }
 
 

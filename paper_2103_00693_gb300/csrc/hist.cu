@@ -38,6 +38,7 @@ struct HistSink {
     uint64_t mask;
     __device__ __forceinline__ uint64_t field(const uint64_t (&z)[W]) const
     {
+        if constexpr (W == 1) return (z[0] >> shift) & mask;
         uint64_t a = 0, b = 0;  // words `word` and `word + 1`, selected without indexing registers
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -132,10 +133,37 @@ __global__ void __launch_bounds__(kThreads) hist_interleaved_kernel(const uint64
         const uint64_t h1 = min(h0 + pl.per_warp, pl.h_end);
         uint64_t z[W];
         seed<W>(t, h0 * kHistG + (uint64_t)lane, z);
-        for (uint64_t h = h0;;) {
+        // Group h + 1 follows group h by the row C_ctz(h+1) (h < 2^59, so
+        // ctz <= 59). Aligned blocks of 2^L groups run as reflected-Gray
+        // blocks over C_0..C_{L-1}, as the reduce's runs do over B_0..B_{U-1}
+        // (shorter blocks for wide rows, which would cost registers).
+        constexpr int L = W == 1 ? 4 : (W <= 4 ? 2 : 1);
+        uint64_t h = h0;
+        while (h < h1 && (h & ((1u << L) - 1))) {
             sink.consume(z);
-            if (++h == h1) break;
-            xor_row<W>(z, s_C[ctz64(h)]);  // h < 2^59, so ctz(h) <= 59
+            if (++h < h1) xor_row<W>(z, s_C[ctz64(h)]);
+        }
+        if (h + (1u << L) <= h1) {
+            if constexpr (W == 1) {
+                uint64_t Cr[L][1];
+#pragma unroll
+                for (int k = 0; k < L; ++k) Cr[k][0] = s_C[k][0];
+                do {
+                    GrayBlock<W, L, uint64_t[L][1], HistSink<W>>::run(z, Cr, sink);
+                    h += 1u << L;
+                    if (h < h1) xor_row<W>(z, s_C[ctz64(h)]);
+                } while (h + (1u << L) <= h1);
+            } else {
+                do {
+                    GrayBlock<W, L, uint64_t[kTableRows - M][W], HistSink<W>>::run(z, s_C, sink);
+                    h += 1u << L;
+                    if (h < h1) xor_row<W>(z, s_C[ctz64(h)]);
+                } while (h + (1u << L) <= h1);
+            }
+        }
+        while (h < h1) {
+            sink.consume(z);
+            if (++h < h1) xor_row<W>(z, s_C[ctz64(h)]);
         }
     }
     __syncthreads();

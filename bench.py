@@ -13,8 +13,11 @@ extra work inside the step and are not counted as solutions).
 
 Other legs on the same JSON line: the dominant kernel's roofline, the store
 kernel's HBM roofline, an end-to-end run through host buffers (e2e), SM
-clocks sampled during the timed region, and the CPU oracle timed on the host
-cores (cpu_baseline). `--impl reference` times the CPU oracle alone.
+clocks sampled during the timed region, the widened rows (dense store,
+histogram), the other single-instance workloads (grid3x3 latency, the grid8x8
+2^40-solution window), the batched and served workloads, and the CPU oracle
+timed on the host cores (cpu_baseline). `--impl reference` times the CPU
+oracle alone.
 """
 
 from __future__ import annotations
@@ -366,6 +369,7 @@ def run_hlf(args, world, rank, local):
             "clocks": clk}
 
     line["next_rows"] = run_next_rows(args, A_dev, n, W, store_n, pk, dev)
+    line["configs"] = run_configs(dev)
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, world, dev, A, r, total, store_n, idx_host)
     del out, smp
@@ -482,6 +486,67 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
     d2h = out_host.numel() * 8 + smp_host.numel() * 8 + red_host.numel() * 8
     return {"value": world * args.steps * total / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / args.steps}
+
+
+def run_configs(dev):
+    """The two other single-instance workloads, through the C ABI:
+    grid3x3 (factor and store every solution, a latency) and grid8x8 (the
+    2^40-solution window reduced on the device, and 2^20 samples of it)."""
+    import statistics as st
+
+    import numpy as np
+    import torch
+
+    from paper_2103_00693_gb300 import hlf
+    from synth import workloads as wl
+
+    out = {}
+    # grid3x3: factor + rank + store of all 2^r solutions + sync, on the host clock
+    A3 = torch.from_numpy(hlf.pack_rows(wl.grid3()).view(np.int64)).to(dev)
+    n3 = A3.shape[0]
+    sols = torch.empty((1 << n3, 1), dtype=torch.int64, device=dev)
+    lat = []
+    for k in range(60):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h = hlf.hlf_factor(A3, n3)
+        r3 = hlf.hlf_get_rank(h)
+        hlf.hlf_enumerate_store(h, 0, 1 << r3, sols)
+        torch.cuda.synchronize(dev)
+        if k >= 10:
+            lat.append(time.perf_counter() - t0)
+        hlf.hlf_destroy(h)
+    out["grid3x3"] = {"workload": "3x3 grid, p=1/2, seed 5: factor + store every solution",
+                      "r": r3, "solutions": 1 << r3, "us_p50": 1e6 * st.median(lat),
+                      "us_min": 1e6 * min(lat)}
+    # grid8x8: reduce of the 2^40 window, and the 2^20 samples
+    A8 = wl.grid8()
+    n8 = A8.shape[0]
+    h = hlf.hlf_factor(torch.from_numpy(hlf.pack_rows(A8).view(np.int64)).to(dev), n8)
+    r8 = hlf.hlf_get_rank(h)
+    off, cnt = wl.grid8_window(min(r8, 64))
+    red = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, device=dev)
+    idx = torch.from_numpy(wl.grid8_samples(off, cnt).view(np.int64)).to(dev)
+    smp = torch.empty(idx.numel(), dtype=torch.int64, device=dev)
+    hlf.hlf_enumerate_reduce(h, off, 1 << 30, red)  # warm-up
+    hlf.hlf_sample(h, idx, idx.numel(), smp)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    e[0].record()
+    hlf.hlf_enumerate_reduce(h, off, cnt, red)
+    e[1].record()
+    hlf.hlf_sample(h, idx, idx.numel(), smp)
+    e[2].record()
+    torch.cuda.synchronize(dev)
+    res = hlf.ReduceResult.from_words(red.cpu().numpy(), 1)
+    if res.count != cnt:
+        raise RuntimeError("grid8x8 window reduce miscounted")
+    hlf.hlf_destroy(h)
+    r_ms, s_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    out["grid8x8"] = {"workload": "8x8 grid, p=1/2, seed 0: 2^40-solution window at a seeded offset",
+                      "r": r8, "solutions": cnt, "reduce_ms": r_ms, "solutions_per_s": cnt / (r_ms / 1e3),
+                      "samples": idx.numel(), "sample_ms": s_ms}
+    return out
 
 
 def run_batched(args):

@@ -103,3 +103,29 @@ def test_dense_one_word_rows(cuda_ok, n):
                 assert np.all(got[lead + words:] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote past the stream"
                 assert np.all(got[:lead] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote before the stream"
     G.close()
+
+
+@pytest.mark.parametrize("n", [100, 129, 1000])
+def test_dense_wide_rows_many_groups(cuda_ok, n):
+    """n > 64 with windows long enough that every warp places many 64-solution
+    groups (the per-lane Gray steps between groups), at an odd offset, with the
+    bulk store (n even) and without (n odd): sampled groups against the oracle,
+    and the ragged last group."""
+    A = synth.random_symmetric(n, 0.02, 500 + n)
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    cnt = (1 << 22) + 37
+    off = synth.window_offset(n, F.space_log2(), cnt) | 1
+    off = min(off, (1 << F.space_log2()) - cnt)
+    out = G.store_dense(off, cnt).cpu().numpy().view(np.uint64)
+    assert len(out) == hlf.dense_words(cnt, n)
+    rng = np.random.default_rng(n)
+    groups = cnt // 64
+    for g in [0, groups - 1] + list(rng.integers(1, groups - 1, size=24)):
+        g = int(g)
+        want = oc.window_dense(F, off + 64 * g, 64)  # 64 solutions = n whole words
+        assert np.array_equal(out[g * n:(g + 1) * n], want), g
+    tail = cnt - 64 * groups
+    want = oc.window_dense(F, off + 64 * groups, tail)
+    assert np.array_equal(out[groups * n:], want)
+    G.close()

@@ -48,20 +48,6 @@ struct Dense1Plan {
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
-// Shifts with PTX semantics: amounts of 64 give 0 (no special case for an
-// empty bit buffer).
-__device__ __forceinline__ uint64_t shl64(uint64_t x, uint32_t s)
-{
-    uint64_t r;
-    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
-    return r;
-}
-__device__ __forceinline__ uint64_t shr64(uint64_t x, uint32_t s)
-{
-    uint64_t r;
-    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
-    return r;
-}
 // Predicated shared-memory store (no branch around it).
 __device__ __forceinline__ void st_shared_if(bool p, uint64_t* a, uint64_t v)
 {

@@ -11,15 +11,12 @@ namespace hlf {
 
 constexpr int kThreads = 256;
 
-// Solutions unrolled per block (2^U): at W = 1, 64 independent hash chains
-// per block give the scheduler an ALU- or FMA-pipe instruction ready in most
-// cycles; beyond W = 1 each solution is already 24W - 4 operations, and
-// deeper unrolling only costs registers (occupancy).
-constexpr int unroll_for(int W) { return W == 1 ? 6 : (W == 2 ? 2 : 1); }
+// Solutions unrolled per Gray block (2^U) in the per-thread walks: 2^6 at
+// W = 1, 2^4 at W = 2, 2^2 at W = 3, 4, and 2 beyond, where each solution is
+// already 24W - 4 operations and deeper unrolling only costs registers.
 // Shape of the single-instance reduce: at W <= 4 one CTA of 1024 threads per
-// SM with up to 64 registers each and a deeper unroll (2^6 solutions per
-// block at W = 1, 2^4 at W = 2, 2^2 at W = 3, 4): measured 7-10% faster than
-// several 256-thread CTAs with 40-44 registers each.
+// SM with up to 64 registers each; with the deeper unroll, measured 7-10%
+// faster than several 256-thread CTAs with 40-44 registers each.
 constexpr int reduce_unroll(int W) { return W == 1 ? 6 : (W == 2 ? 4 : (W <= 4 ? 2 : 1)); }
 constexpr int reduce_threads(int W) { return W <= 4 ? 1024 : kThreads; }
 constexpr int min_ctas_for(int W) { return W <= 4 ? 1 : 2; }
@@ -66,6 +63,19 @@ __device__ __forceinline__ void load_table_hash_domain(Table<W>& t, const uint64
     }
 }
 
+// 64-bit shifts with PTX semantics: amounts of 64 give 0.
+__device__ __forceinline__ uint64_t shl64(uint64_t x, uint32_t s)
+{
+    uint64_t r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+__device__ __forceinline__ uint64_t shr64(uint64_t x, uint32_t s)
+{
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
 template <int W>
 __device__ __forceinline__ void xor_row(uint64_t (&z)[W], const uint64_t* __restrict__ b)
 {

@@ -239,7 +239,7 @@ template <int W>
 hlf_status launch_reduce_chunks_w(const uint64_t* table, uint64_t offset, uint64_t chunk, uint64_t n_chunks,
                                   hlf_reduce* out, cudaStream_t s)
 {
-    constexpr int U = unroll_for(W);
+    constexpr int U = reduce_unroll(W);
     const uint64_t cap = (uint64_t)sm_count() * blocks_per_sm(reduce_chunks_kernel<W, U>, 0);
     const unsigned blocks = (unsigned)(n_chunks < cap ? n_chunks : cap);
     reduce_chunks_kernel<W, U><<<blocks, kThreads, 0, s>>>(table, offset, chunk, n_chunks, out);

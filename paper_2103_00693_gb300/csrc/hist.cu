@@ -15,10 +15,13 @@
 // - per-thread runs (the reduce's walk, enum_impl.cuh), for fields the first
 //   five rows leave (nearly) unchanged: there the interleaved lanes would all
 //   hit one bin, while a thread's run stays in one bin for many solutions.
-// Each solution's bits [lo, lo + nbits) select a bin. Up to 2^14 bins live in
-// shared memory per CTA (32-bit counters, flushed to the global 64-bit bins
-// with one atomic per nonzero bin); wider fields count straight into global
-// memory.
+// Each solution's bits [lo, lo + nbits) select a bin. They lie in at most
+// two words of the solution, and XOR acts word by word, so the kernels walk
+// the projection of the table onto those words (P = 1 or 2 words per row,
+// whatever n is) and the field starts in the first projected word. Up to
+// 2^14 bins live in shared memory per CTA (32-bit counters, flushed to the
+// global 64-bit bins with one atomic per nonzero bin); wider fields count
+// straight into global memory.
 
 #include "enum_impl.cuh"
 
@@ -30,32 +33,36 @@ constexpr int kHistG = 32;                              // consecutive indices p
 constexpr uint64_t kHistMaxGroupsPerWarp = 1ull << 23;  // keeps a CTA's counts below 2^32
 constexpr uint64_t kHistMaxPerThread = 1ull << 23;      // the same bound for the run walk
 
-template <int W>
+template <int P>
 struct HistSink {
     uint32_t* s_bins;               // shared, when nbits <= kHistSmemBits
     unsigned long long* g_bins;     // global, otherwise
-    int word, shift, nbits;
+    uint32_t shift;                 // the field's first bit in projected word 0
+    int nbits;
     uint64_t mask;
-    __device__ __forceinline__ uint64_t field(const uint64_t (&z)[W]) const
+    __device__ __forceinline__ uint64_t field(const uint64_t (&z)[P]) const
     {
-        if constexpr (W == 1) return (z[0] >> shift) & mask;
-        uint64_t a = 0, b = 0;  // words `word` and `word + 1`, selected without indexing registers
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            if (k == word) a = z[k];
-            if (k == word + 1) b = z[k];
-        }
-        uint64_t v = a >> shift;
-        if (shift) v |= b << (64 - shift);
+        uint64_t v = z[0] >> shift;
+        if constexpr (P == 2) v |= shl64(z[1], 64 - shift);  // 0 when shift == 0
         return v & mask;
     }
-    __device__ __forceinline__ void consume(const uint64_t (&z)[W])
+    __device__ __forceinline__ void consume(const uint64_t (&z)[P])
     {
         const uint64_t v = field(z);
         if (nbits <= kHistSmemBits) atomicAdd(&s_bins[v], 1u);
         else atomicAdd(&g_bins[v], 1ull);
     }
 };
+
+// The table's rows (and z0) projected onto words [word, word + P).
+template <int P>
+__device__ __forceinline__ void load_table_projected(Table<P>& t, const uint64_t* __restrict__ g, int Wfull,
+                                                     int word)
+{
+    uint64_t* d = &t.B[0][0];
+    for (int i = threadIdx.x; i < kTableTotalRows * P; i += blockDim.x)
+        d[i] = g[(i / P) * Wfull + word + i % P];
+}
 
 struct HistPlan {
     uint64_t offset, count;
@@ -67,6 +74,7 @@ struct HistPlan {
     uint64_t per_warp;    // groups per warp
     uint64_t per_thread;  // the run walk: [offset + g * per_thread, ...) for threads g < used
     uint64_t used;
+    int Wfull, word;      // the table's words per row; the first projected word
 };
 
 // True when the field bits of B_0..B_4 are linearly independent over GF(2).
@@ -104,13 +112,13 @@ __global__ void __launch_bounds__(kThreads) hist_interleaved_kernel(const uint64
     __shared__ Table<W> t;
     __shared__ uint64_t s_C[kTableRows - M][W];  // C_j = B_{M-1} ^ B_{M+j}
     __shared__ bool s_skip;
-    load_table<W>(t, table);
+    load_table_projected<W>(t, table, pl.Wfull, pl.word);
     const bool in_smem = nbits <= kHistSmemBits;
     const uint32_t nb = 1u << nbits;
     if (in_smem)
         for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) s_bins[i] = 0;
     __syncthreads();
-    HistSink<W> sink{s_bins, out, lo >> 6, lo & 63, nbits, nbits == 64 ? ~0ull : ((1ull << nbits) - 1)};
+    HistSink<W> sink{s_bins, out, (uint32_t)(lo & 63), nbits, nbits == 64 ? ~0ull : ((1ull << nbits) - 1)};
     if (threadIdx.x == 0) s_skip = !fields_independent<W>(t, sink);  // the run walk's case
     for (int i = threadIdx.x; i < (kTableRows - M) * W; i += blockDim.x) {
         const int j = i / W, w = i % W;
@@ -180,13 +188,13 @@ __global__ void __launch_bounds__(kThreads) hist_runs_kernel(const uint64_t* __r
     extern __shared__ uint32_t s_bins[];
     __shared__ Table<W> t;
     __shared__ bool s_skip;
-    load_table<W>(t, table);
+    load_table_projected<W>(t, table, pl.Wfull, pl.word);
     const bool in_smem = nbits <= kHistSmemBits;
     const uint32_t nb = 1u << nbits;
     if (in_smem)
         for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) s_bins[i] = 0;
     __syncthreads();
-    HistSink<W> sink{s_bins, out, lo >> 6, lo & 63, nbits, nbits == 64 ? ~0ull : ((1ull << nbits) - 1)};
+    HistSink<W> sink{s_bins, out, (uint32_t)(lo & 63), nbits, nbits == 64 ? ~0ull : ((1ull << nbits) - 1)};
     if (threadIdx.x == 0) s_skip = fields_independent<W>(t, sink);  // the interleaved walk's case
     __syncthreads();
     if (s_skip) return;
@@ -214,13 +222,15 @@ hlf_status hist_attrs(K kernel, size_t smem, int* per_sm)
 }
 
 template <int W>
-hlf_status launch_hist_w(const uint64_t* table, uint64_t offset, uint64_t count, int lo, int nbits,
+hlf_status launch_hist_w(const uint64_t* table, int Wfull, uint64_t offset, uint64_t count, int lo, int nbits,
                          uint64_t* out, cudaStream_t s)
 {
-    constexpr int U = unroll_for(W);
+    constexpr int U = reduce_unroll(W);
     HistPlan pl{};
     pl.offset = offset;
     pl.count = count;
+    pl.Wfull = Wfull;
+    pl.word = lo >> 6;
     // Full groups are [h_first * 32, h_end * 32); the window's end can be 2^64
     // exactly (r >= 64), which wraps to 0 in 64 bits.
     const uint64_t G = kHistG;
@@ -296,25 +306,10 @@ hlf_status launch_hist_w(const uint64_t* table, uint64_t offset, uint64_t count,
 hlf_status launch_histogram(const uint64_t* table, int W, uint64_t offset, uint64_t count, int lo, int nbits,
                             uint64_t* out, cudaStream_t s)
 {
-    switch (W) {
-    case 1: return launch_hist_w<1>(table, offset, count, lo, nbits, out, s);
-    case 2: return launch_hist_w<2>(table, offset, count, lo, nbits, out, s);
-    case 3: return launch_hist_w<3>(table, offset, count, lo, nbits, out, s);
-    case 4: return launch_hist_w<4>(table, offset, count, lo, nbits, out, s);
-    case 5: return launch_hist_w<5>(table, offset, count, lo, nbits, out, s);
-    case 6: return launch_hist_w<6>(table, offset, count, lo, nbits, out, s);
-    case 7: return launch_hist_w<7>(table, offset, count, lo, nbits, out, s);
-    case 8: return launch_hist_w<8>(table, offset, count, lo, nbits, out, s);
-    case 9: return launch_hist_w<9>(table, offset, count, lo, nbits, out, s);
-    case 10: return launch_hist_w<10>(table, offset, count, lo, nbits, out, s);
-    case 11: return launch_hist_w<11>(table, offset, count, lo, nbits, out, s);
-    case 12: return launch_hist_w<12>(table, offset, count, lo, nbits, out, s);
-    case 13: return launch_hist_w<13>(table, offset, count, lo, nbits, out, s);
-    case 14: return launch_hist_w<14>(table, offset, count, lo, nbits, out, s);
-    case 15: return launch_hist_w<15>(table, offset, count, lo, nbits, out, s);
-    case 16: return launch_hist_w<16>(table, offset, count, lo, nbits, out, s);
-    default: return HLF_ERR_SIZE;
-    }
+    if (W < 1 || W > HLF_MAX_W || lo < 0 || nbits < 1 || lo + nbits > 64 * W) return HLF_ERR_ARG;
+    // the field's words: one, or two when it crosses a word boundary
+    if ((lo & 63) + nbits > 64) return launch_hist_w<2>(table, W, offset, count, lo, nbits, out, s);
+    return launch_hist_w<1>(table, W, offset, count, lo, nbits, out, s);
 }
 
 }  // namespace hlf

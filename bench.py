@@ -59,9 +59,9 @@ KERNEL_SOURCES = {
     "dense1_kernel<16,1,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
-    "reduce_kernel<1,6,1024>": {"bytes": 897280 + 0, "sources": "12d473f308918f62"},
-    "store_kernel<1,2>": {"bytes": 167936 + 8524608768, "sources": "12d473f308918f62"},
-    "dense1_kernel<16,1,1>": {"bytes": 89600 + 4766977024, "sources": "924d50e6b2f3fffd"},
+    "reduce_kernel<1,6,1024>": {"bytes": 936960 + 0, "sources": "e2167929a4b62a09"},
+    "store_kernel<1,2>": {"bytes": 236288 + 8525072128, "sources": "e2167929a4b62a09"},
+    "dense1_kernel<16,1,1>": {"bytes": 93184 + 4767062272, "sources": "79a16e1586c3ae3b"},
 }
 
 

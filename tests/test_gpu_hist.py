@@ -86,3 +86,18 @@ def test_histogram_both_walks(cuda_ok, order):
             assert np.array_equal(got, oc.histogram(F, off, cnt, lo, nb, order)), (order, lo, nb, off, cnt)
     assert seen == {True, False}, "both walks should be exercised"
     G.close()
+
+
+def test_histogram_window_ending_at_2_64(cuda_ok):
+    """r > 64: the index space is [0, 2^64), and a window may end exactly at
+    2^64 (the end wraps to 0 in 64-bit arithmetic); both walks."""
+    A = synth.random_symmetric(100, 0.02, 140)
+    F = oc.factor(A)
+    assert F.r > 64
+    G = hlf.Factorization.from_dense(A)
+    for cnt in (1, 31, 32, 33, 5000, 70001):
+        off = (1 << 64) - cnt
+        for lo, nb in ((0, 12), (70, 9), (40, 14)):
+            got = G.histogram(off, cnt, lo, nb).cpu().numpy().view(np.uint64)
+            assert np.array_equal(got, oc.histogram(F, off, cnt, lo, nb)), (cnt, lo, nb)
+    G.close()

@@ -125,10 +125,12 @@ def pack_rows(A: np.ndarray) -> np.ndarray:
     A = np.asarray(A, dtype=np.uint8)
     rows, n = A.shape
     W = words(n)
-    padded = np.zeros((rows, W * 64), dtype=np.uint8)
-    padded[:, :n] = A
-    bits = np.packbits(padded.reshape(rows, W, 64), axis=2, bitorder="little")  # [rows, W, 8]
-    return bits.view("<u8").reshape(rows, W).astype(np.uint64)
+    b = np.packbits(A, axis=1, bitorder="little")  # [rows, ceil(n / 8)], bits past n are 0
+    if b.shape[1] != W * 8:
+        full = np.zeros((rows, W * 8), dtype=np.uint8)
+        full[:, :b.shape[1]] = b
+        b = full
+    return np.ascontiguousarray(b).view("<u8").reshape(rows, W).astype(np.uint64)
 
 
 def unpack_rows(words_: np.ndarray, n: int) -> np.ndarray:

@@ -128,6 +128,7 @@ class Req:
     blk_dev: list | None = None
     blk_host: list | None = None
     blk_in: list | None = None
+    blk_mat: list | None = None
     A_dev: object = None
     ev_factor: object = None
     ev_copy: object = None
@@ -197,6 +198,9 @@ class Server:
         self.dev_ring = Ring(torch.empty(device_bytes // 8, dtype=torch.int64, device="cuda"))
         self.host_ring = Ring(torch.empty(host_bytes // 8, dtype=torch.int64, pin_memory=True))
         self.in_ring = Ring(torch.empty((64 << 20) // 8, dtype=torch.int64, pin_memory=True))
+        # the packed matrices on the device: carved from a ring as well, so
+        # the loop never reaches the allocator (which may synchronise)
+        self.mat_ring = Ring(torch.empty((64 << 20) // 8, dtype=torch.int64, device="cuda"))
 
     def close(self):
         if self.many:
@@ -223,17 +227,20 @@ class Server:
             self.dev_ring.free(bd)
             return False
         bi = self.in_ring.alloc(q.n * q.W)
-        if bi is None:
+        bm = self.mat_ring.alloc(q.n * q.W) if bi is not None else None
+        if bm is None:
+            if bi is not None:
+                self.in_ring.free(bi)
             self.dev_ring.free(bd)
             self.host_ring.free(bh)
             return False
-        q.blk_dev, q.blk_host, q.blk_in = bd, bh, bi
+        q.blk_dev, q.blk_host, q.blk_in, q.blk_mat = bd, bh, bi, bm
         staged = self.in_ring.view(bi, q.n * q.W)
         staged.copy_(torch.from_numpy(hlf.pack_rows(q.A).view(np.int64).ravel()))
         sf = self.s_factors[self._next_factor]
         self._next_factor = (self._next_factor + 1) % len(self.s_factors)
         with torch.cuda.stream(sf):
-            q.A_dev = torch.empty((q.n, q.W), dtype=torch.int64, device="cuda")
+            q.A_dev = self.mat_ring.view(bm, q.n * q.W).view(q.n, q.W)
             q.A_dev.view(-1).copy_(staged, non_blocking=True)
             q.h = hlf.hlf_factor(q.A_dev, q.n, sf)
             q.ev_factor = torch.cuda.Event()
@@ -302,6 +309,7 @@ class Server:
                 hlf.hlf_destroy(q.h)
                 q.h = 0
                 q.A_dev = None
+                self.mat_ring.free(q.blk_mat)  # the factor kernel read it long before the copy ended
                 self.dev_ring.free(q.blk_dev)
                 self.host_ring.free(q.blk_host)
                 done.append(q)
@@ -313,8 +321,9 @@ class Server:
                     dt = waiting[0].t_arrival - (time.perf_counter() - t0)
                     if dt > 0:
                         time.sleep(min(dt, 0.001))
-                else:
-                    time.sleep(10e-6)
+                # with work in flight the loop polls its events without
+                # sleeping: a sleep of a few microseconds lasts ~60 us on
+                # Linux, which would add to every request's latency
         st.makespan_s = time.perf_counter() - t0
         if busy_since is not None:
             st.busy_s += st.makespan_s - busy_since

@@ -12,12 +12,12 @@ namespace hlf {
 constexpr int kThreads = 256;
 
 // Solutions unrolled per Gray block (2^U) in the per-thread walks: 2^6 at
-// W = 1, 2^4 at W = 2, 2^2 at W = 3, 4, and 2^1 beyond, where each solution is
+// W = 1, 2^4 at W = 2, 2^3 at W = 3, 4, and 2^1 beyond, where each solution is
 // already 24W - 4 operations and deeper unrolling only costs registers.
 // Shape of the single-instance reduce: at W <= 4 one CTA of 1024 threads per
 // SM with up to 64 registers each; with the deeper unroll, measured 7-10%
 // faster than several 256-thread CTAs with 40-44 registers each.
-constexpr int reduce_unroll(int W) { return W == 1 ? 6 : (W == 2 ? 4 : (W <= 4 ? 2 : 1)); }
+constexpr int reduce_unroll(int W) { return W == 1 ? 6 : (W == 2 ? 4 : (W <= 4 ? 3 : 1)); }
 constexpr int reduce_threads(int W) { return W <= 4 ? 1024 : kThreads; }
 constexpr int min_ctas_for(int W) { return W <= 4 ? 1 : 2; }
 

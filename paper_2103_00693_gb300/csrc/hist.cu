@@ -28,29 +28,55 @@
 namespace hlf {
 namespace {
 
-constexpr int kHistSmemBits = 14;
+constexpr int kHistSmemBits = 15;  // 2^15 32-bit bins: 128 KB of shared memory
 constexpr int kHistG = 32;                              // consecutive indices per warp step
 constexpr uint64_t kHistMaxGroupsPerWarp = 1ull << 23;  // keeps a CTA's counts below 2^32
 constexpr uint64_t kHistMaxPerThread = 1ull << 23;      // the same bound for the run walk
 
-template <int P>
+// Coalesce (the run walk with bins in global memory): repeats of the current
+// bin are counted in a register and added with one atomic when the bin
+// changes, and flush() adds the last count. A field the first rows leave
+// unchanged keeps one bin for long stretches of a thread's run, and global
+// atomics on one address would serialise.
+template <int P, bool Coalesce = false>
 struct HistSink {
     uint32_t* s_bins;               // shared, when nbits <= kHistSmemBits
     unsigned long long* g_bins;     // global, otherwise
     uint32_t shift;                 // the field's first bit in projected word 0
     int nbits;
     uint64_t mask;
+    uint64_t cur = 0;               // Coalesce: the current bin and its pending count
+    uint32_t pending = 0;
     __device__ __forceinline__ uint64_t field(const uint64_t (&z)[P]) const
     {
         uint64_t v = z[0] >> shift;
         if constexpr (P == 2) v |= shl64(z[1], 64 - shift);  // 0 when shift == 0
         return v & mask;
     }
+    __device__ __forceinline__ void add(uint64_t v, uint32_t c)
+    {
+        if (nbits <= kHistSmemBits) atomicAdd(&s_bins[v], c);
+        else atomicAdd(&g_bins[v], (unsigned long long)c);
+    }
     __device__ __forceinline__ void consume(const uint64_t (&z)[P])
     {
         const uint64_t v = field(z);
-        if (nbits <= kHistSmemBits) atomicAdd(&s_bins[v], 1u);
-        else atomicAdd(&g_bins[v], 1ull);
+        if constexpr (Coalesce) {
+            if (v == cur) {
+                ++pending;
+            } else {
+                if (pending) add(cur, pending);
+                cur = v;
+                pending = 1;
+            }
+        } else {
+            add(v, 1u);
+        }
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (Coalesce && pending) add(cur, pending);
+        pending = 0;
     }
 };
 
@@ -79,7 +105,7 @@ struct HistPlan {
 
 // True when the field bits of B_0..B_4 are linearly independent over GF(2).
 template <int W>
-__device__ bool fields_independent(const Table<W>& t, const HistSink<W>& sink)
+__device__ bool fields_independent(const Table<W>& t, const HistSink<W, false>& sink)
 {
     uint64_t basis[5];
     int r = 0;
@@ -181,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) hist_interleaved_kernel(const uint64
 }
 
 // The per-thread run walk.
-template <int W, int U>
+template <int W, int U, bool Coalesce>
 __global__ void __launch_bounds__(kThreads) hist_runs_kernel(const uint64_t* __restrict__ table, HistPlan pl,
                                                              int lo, int nbits, unsigned long long* __restrict__ out)
 {
@@ -194,14 +220,19 @@ __global__ void __launch_bounds__(kThreads) hist_runs_kernel(const uint64_t* __r
     if (in_smem)
         for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) s_bins[i] = 0;
     __syncthreads();
-    HistSink<W> sink{s_bins, out, (uint32_t)(lo & 63), nbits, nbits == 64 ? ~0ull : ((1ull << nbits) - 1)};
-    if (threadIdx.x == 0) s_skip = fields_independent<W>(t, sink);  // the interleaved walk's case
+    const uint64_t mask = nbits == 64 ? ~0ull : ((1ull << nbits) - 1);
+    if (threadIdx.x == 0)  // the interleaved walk's case
+        s_skip = fields_independent<W>(t, HistSink<W, false>{s_bins, out, (uint32_t)(lo & 63), nbits, mask});
     __syncthreads();
     if (s_skip) return;
+    HistSink<W, Coalesce> sink{s_bins, out, (uint32_t)(lo & 63), nbits, mask};
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g < pl.used) {
         const uint64_t a = g * pl.per_thread;
-        if (a < pl.count) walk_run<W, U, HistSink<W>>(t, pl.offset + a, min(pl.per_thread, pl.count - a), sink);
+        if (a < pl.count) {
+            walk_run<W, U, HistSink<W, Coalesce>>(t, pl.offset + a, min(pl.per_thread, pl.count - a), sink);
+            sink.flush();
+        }
     }
     __syncthreads();
     if (in_smem)
@@ -261,7 +292,9 @@ hlf_status launch_hist_w(const uint64_t* table, int Wfull, uint64_t offset, uint
         per_sm_r = fit[dev][1];
     } else {
         hlf_status st = hist_attrs(hist_interleaved_kernel<W>, smem, &per_sm_i);
-        if (st == HLF_OK) st = hist_attrs(hist_runs_kernel<W, U>, smem, &per_sm_r);
+        if (st == HLF_OK)
+            st = smem ? hist_attrs(hist_runs_kernel<W, U, false>, smem, &per_sm_r)
+                      : hist_attrs(hist_runs_kernel<W, U, true>, smem, &per_sm_r);
         if (st != HLF_OK) return st;
         if (dev < 64 && smem == (sizeof(uint32_t) << kHistSmemBits)) {
             fit[dev][0] = per_sm_i;
@@ -297,7 +330,10 @@ hlf_status launch_hist_w(const uint64_t* table, int Wfull, uint64_t offset, uint
     auto* o = reinterpret_cast<unsigned long long*>(out);
     hist_interleaved_kernel<W><<<(unsigned)blocks_i, kThreads, smem, s>>>(table, pl, lo, nbits, o);
     if (cudaGetLastError() != cudaSuccess) return HLF_ERR_CUDA;
-    hist_runs_kernel<W, U><<<(unsigned)blocks_r, kThreads, smem, s>>>(table, pl, lo, nbits, o);
+    if (smem)
+        hist_runs_kernel<W, U, false><<<(unsigned)blocks_r, kThreads, smem, s>>>(table, pl, lo, nbits, o);
+    else  // bins in global memory: coalesce repeats
+        hist_runs_kernel<W, U, true><<<(unsigned)blocks_r, kThreads, smem, s>>>(table, pl, lo, nbits, o);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 

@@ -156,9 +156,10 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
  * [t*n, (t+1)*n) of the stream at out_dev, where stream bit b is bit b % 64
  * of word b / 64 and solution bit j is z_{j+1}. Bits past the last solution
  * in the last word are written as 0.
- * out_dev: device, caller-owned, ceil(count * n / 64) uint64, 8-byte aligned.
- * Same range rule as hlf_enumerate_store. For n = 36 this writes 36 bits per
- * solution instead of 64.
+ * out_dev: device, caller-owned, ceil(count * n / 64) uint64, 8-byte aligned
+ * (a 16-byte aligned out_dev is written with bulk TMA stores, which is
+ * faster). Same range rule as hlf_enumerate_store. For n = 36 this writes 36
+ * bits per solution instead of 64.
  */
 hlf_status hlf_enumerate_store_dense(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev,
                                      void* stream);

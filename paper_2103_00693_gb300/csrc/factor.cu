@@ -12,7 +12,7 @@ template <int W>
 constexpr int rows_per_thread() { return W <= 8 ? 1 : 2; }
 
 template <int W>
-__global__ void __launch_bounds__(512) factor_kernel(const uint64_t* __restrict__ A, int n, FactorOut o)
+__global__ void __launch_bounds__(512, 1) factor_kernel(const uint64_t* __restrict__ A, int n, FactorOut o)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     factor_block<W, rows_per_thread<W>(), HLF_MAX_N>(A, n, o, smem);

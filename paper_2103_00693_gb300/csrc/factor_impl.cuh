@@ -5,15 +5,24 @@
 //       A in registers (W uint64 words each). For each column c, left to
 //       right, the candidates are the rows not yet used as a pivot that have
 //       bit c set; a min over each warp and then over the warps picks the
-//       lowest such row p. Each warp stages its lowest candidate's words next
-//       to its index, so one barrier per column suffices: after it every
-//       thread knows p and reads row p from its warp's slot, and every other
+//       lowest such row p. The key minimised is (row << 5) | warp, so the
+//       minimum also names the warp that holds row p. Each warp stages its
+//       lowest candidate's words next to its key, so one barrier per column
+//       suffices: after it every thread knows p and reads row p from that
+//       warp's slot, and every other
 //       row with bit c set XORs it in (rows above and below: Gauss-Jordan, so
 //       the result is the unique reduced row echelon form). The slots
 //       alternate with the column's parity, so a slot is rewritten only after
-//       the next column's barrier, when every read of it is done. Rows are
-//       never swapped; the pivot row of column c is remembered instead.
-//       Unused rows end at zero.
+//       the next column's barrier, when every read of it is done. A row not
+//       yet used as a pivot is zero in every column left of c (each earlier
+//       column was cleared by its pivot or had no candidate), so the pivot
+//       row's words left of c's word are zero: they are neither staged nor
+//       XORed. Rows are never swapped; the pivot row of column c is
+//       remembered instead. Unused rows end at zero.
+//
+//       Measured and rejected: one warp eliminating alone with ballots and
+//       shuffles (slower from W = 2 on), and two columns per barrier (three
+//       minima per warp; more work per column than the barrier it saves).
 //   (2)-(4) Kernel basis, q and z^a. For a free column f the kernel vector is
 //       x_f = e_f + sum_k B_k[f] e_{p_k}; q(x_f) = sum over i in supp(x_f) of
 //       popcount(A_i & x_f), mod 4, which is x_f^T A x_f mod 4. With z^a
@@ -21,7 +30,8 @@
 //       2 z^T x_f = q(x_f) (mod 4) gives z^a_f = q(x_f) / 2 directly.
 //
 // Also checked here: padding bits (column >= n) are zero and A is symmetric
-// (Section 1 defines the problem for symmetric A only).
+// (Section 1 defines the problem for symmetric A only), the latter by 64 x 64
+// bit-block transposes in registers.
 #pragma once
 
 #include "hlf_internal.cuh"
@@ -38,6 +48,36 @@ struct FactorSmem {
     uint64_t z0[W];
     int err;
 };
+
+// Transpose a 64 x 64 bit block held by one warp: lane l has rows l (x0) and
+// l + 32 (x1), bit s of a row being column s. Each stage j swaps bit j of the
+// row index with bit j of the column index, i.e. exchanges the bits at column
+// s + j of row t with those at column s of row t + j (bit j of s and of t
+// clear); the six stages compose to the transpose. Stage 32 pairs the two rows
+// of a lane, the others pair lanes l and l ^ j.
+__device__ __forceinline__ void transpose64_warp(uint64_t& x0, uint64_t& x1, int lane)
+{
+    {
+        const uint64_t t = ((x0 >> 32) ^ x1) & 0x00000000FFFFFFFFull;
+        x1 ^= t;
+        x0 ^= t << 32;
+    }
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        const uint64_t m = j == 16 ? 0x0000FFFF0000FFFFull
+                         : j == 8  ? 0x00FF00FF00FF00FFull
+                         : j == 4  ? 0x0F0F0F0F0F0F0F0Full
+                         : j == 2  ? 0x3333333333333333ull
+                                   : 0x5555555555555555ull;
+        const bool upper = (lane & j) != 0;  // this lane's rows are the t + j of their pairs
+        const uint64_t o0 = __shfl_xor_sync(0xffffffffu, x0, j);
+        const uint64_t o1 = __shfl_xor_sync(0xffffffffu, x1, j);
+        const uint64_t t0 = upper ? (((o0 >> j) ^ x0) & m) : (((x0 >> j) ^ o0) & m);
+        const uint64_t t1 = upper ? (((o1 >> j) ^ x1) & m) : (((x1 >> j) ^ o1) & m);
+        x0 ^= upper ? t0 : t0 << j;
+        x1 ^= upper ? t1 : t1 << j;
+    }
+}
 
 template <int W, int MAXN>
 constexpr size_t factor_smem_bytes(int n)
@@ -70,37 +110,38 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
         const int i = tid + j * bs;
 #pragma unroll
         for (int w = 0; w < W; ++w) row[j][w] = i < n ? A[(size_t)i * W + w] : 0ull;
-        if (i < n) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) s_rows[i * W + w] = row[j][w];
-        }
     }
     if (tid == 0) sm.err = 0;
     if (tid < W) sm.z0[tid] = 0;
     for (int i = tid; i < MAXN / 32; i += bs) sm.pivmask[i] = 0;
     __syncthreads();
 
-    // ---- input checks: padding, then symmetry (bit j of row i == bit i of row j)
+    // ---- input checks: padding bits, then symmetry. A warp takes the 64 x 64
+    // blocks (I, J) and (J, I), I <= J, of the W x W block grid, transposes the
+    // first in registers and compares it with the second on the rows and
+    // columns below n.
     int bad = 0;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        const int i = tid + j * bs;
-        if (i >= n) continue;
         const int tail = n & 63;
-        if (tail && (row[j][W - 1] >> tail)) bad = HLF_ERR_PADDING;
-        const int wi = i >> 6;
-        const int bi = i & 63;
-        if (bad) continue;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            uint64_t t = 0;
-            for (int b = 0; b < 64; ++b) {
-                const int c = (w << 6) + b;
-                if (c >= n) break;
-                t |= ((s_rows[c * W + wi] >> bi) & 1ull) << b;
-            }
-            if (t != row[j][w]) bad = HLF_ERR_NOT_SYMMETRIC;
+        if (tid + j * bs < n && tail && (row[j][W - 1] >> tail)) bad = HLF_ERR_PADDING;
+    }
+    for (int pr = warp; pr < W * (W + 1) / 2; pr += nwarps) {
+        int I = 0, rest = pr;  // pair index -> (I, J), I <= J < W
+        while (rest >= W - I) {
+            rest -= W - I;
+            ++I;
         }
+        const int J = I + rest;
+        const int ra = 64 * I + lane, rb = 64 * J + lane;
+        uint64_t p0 = ra < n ? A[(size_t)ra * W + J] : 0ull;
+        uint64_t p1 = ra + 32 < n ? A[(size_t)(ra + 32) * W + J] : 0ull;
+        const uint64_t q0 = rb < n ? A[(size_t)rb * W + I] : 0ull;
+        const uint64_t q1 = rb + 32 < n ? A[(size_t)(rb + 32) * W + I] : 0ull;
+        transpose64_warp(p0, p1, lane);
+        const int cols = n - 64 * I;
+        const uint64_t cm = cols >= 64 ? ~0ull : ((1ull << cols) - 1ull);
+        if ((rb < n && ((p0 ^ q0) & cm)) || (rb + 32 < n && ((p1 ^ q1) & cm))) bad = max(bad, HLF_ERR_NOT_SYMMETRIC);
     }
     if (bad) atomicMax(&sm.err, bad);
     __syncthreads();
@@ -114,75 +155,87 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
         return -1;
     }
 
-    // ---- (1) Gauss-Jordan elimination
-    bool used[R];
-    int my_k[R];
+    // ---- (1) Gauss-Jordan elimination: B_k to s_rows[k][.], its pivot column to sm.pivcol[k]
+    int r;
+    {
+        bool used[R];
+        int my_k[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        used[j] = false;
-        my_k[j] = -1;
-    }
-    int rank = 0;
+        for (int j = 0; j < R; ++j) {
+            used[j] = false;
+            my_k[j] = -1;
+        }
+        int rank = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-        for (int b = 0; b < 64; ++b) {
-            const int c = (w << 6) + b;
-            if (c >= n) break;
-            const int buf = c & 1;
-            int cand = kNone;  // this thread's lowest unused row with bit c
+        for (int w = 0; w < W; ++w) {
+            for (int b = 0; b < 64; ++b) {
+                const int c = (w << 6) + b;
+                if (c >= n) break;
+                const int buf = c & 1;
+                // this thread's lowest unused row with bit c, keyed (row << 5) | warp
+                int cand = kNone;
 #pragma unroll
-            for (int j = R - 1; j >= 0; --j)
-                if (tid + j * bs < n && !used[j] && ((row[j][w] >> b) & 1ull)) cand = tid + j * bs;
-            const int wmin = __reduce_min_sync(0xffffffffu, cand);
-            if (wmin != kNone && cand == wmin) {  // this lane holds the warp's lowest candidate
+                for (int j = R - 1; j >= 0; --j)
+                    if (tid + j * bs < n && !used[j] && ((row[j][w] >> b) & 1ull)) cand = ((tid + j * bs) << 5) | warp;
+                const int wmin = __reduce_min_sync(0xffffffffu, cand);
+                if (wmin != kNone && cand == wmin) {  // this lane holds the warp's lowest candidate
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        if (tid + j * bs != (wmin >> 5)) continue;
+#pragma unroll
+                        for (int v = w; v < W; ++v) sm.crow[buf][warp][v] = row[j][v];
+                    }
+                }
+                if (lane == 0) sm.first[buf][warp] = wmin;
+                __syncthreads();
+                int pk = lane < nwarps ? sm.first[buf][lane] : kNone;
+                pk = __reduce_min_sync(0xffffffffu, pk);
+                if (pk == kNone) continue;  // no pivot in column c (uniform)
+                const uint64_t* prow = sm.crow[buf][pk & 31];
+                const int p = pk >> 5;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    if (tid + j * bs != wmin) continue;
-#pragma unroll
-                    for (int v = 0; v < W; ++v) sm.crow[buf][warp][v] = row[j][v];
+                    if (tid + j * bs == p) {
+                        used[j] = true;
+                        my_k[j] = rank;
+                    }
                 }
-            }
-            if (lane == 0) sm.first[buf][warp] = wmin;
-            __syncthreads();
-            int p = lane < nwarps ? sm.first[buf][lane] : kNone;
-            p = __reduce_min_sync(0xffffffffu, p);
-            if (p == kNone) continue;  // no pivot in column c (uniform)
-            const uint64_t* prow = sm.crow[buf][(p % bs) >> 5];
-            if (tid == p % bs) {
-                const int pj = p / bs;
+                if (tid == 0) sm.pivcol[rank] = c;
+                if constexpr (R == 1) {  // row p; its words below word w are zero
+                    uint64_t pv[W];
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    if (j != pj) continue;
-                    used[j] = true;
-                    my_k[j] = rank;
+                    for (int v = w; v < W; ++v) pv[v] = prow[v];
+                    const uint64_t m = (tid != p && ((row[0][w] >> b) & 1ull)) ? ~0ull : 0ull;
+#pragma unroll
+                    for (int v = w; v < W; ++v) row[0][v] ^= pv[v] & m;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        if (tid + j * bs != p && ((row[j][w] >> b) & 1ull)) {
+#pragma unroll
+                            for (int v = w; v < W; ++v) row[j][v] ^= prow[v];
+                        }
+                    }
                 }
+                ++rank;
             }
-            if (tid == 0) sm.pivcol[rank] = c;
+        }
+        r = rank;
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                if (tid + j * bs != p && ((row[j][w] >> b) & 1ull)) {
+        for (int j = 0; j < R; ++j) {
+            if (!used[j]) continue;
 #pragma unroll
-                    for (int v = 0; v < W; ++v) row[j][v] ^= prow[v];
-                }
-            }
-            ++rank;
+            for (int v = 0; v < W; ++v) s_rows[my_k[j] * W + v] = row[j][v];
         }
     }
-    const int r = rank;
     const int nb = r < HLF_MAX_VARYING ? r : HLF_MAX_VARYING;
-    __syncthreads();  // all reads of the input rows in s_rows are done
+    __syncthreads();
 
     // ---- outputs of step (1): B_k in pivot order, pivots, enumeration table
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        if (!used[j]) continue;
-        const int k = my_k[j];
-#pragma unroll
-        for (int v = 0; v < W; ++v) {
-            s_rows[k * W + v] = row[j][v];
-            if (o.basis) o.basis[(size_t)k * W + v] = row[j][v];
-            if (k < HLF_MAX_VARYING) o.table[k * W + v] = row[j][v];
-        }
+    for (int i = tid; i < r * W; i += bs) {
+        const uint64_t v = s_rows[i];
+        if (o.basis) o.basis[i] = v;
+        if (i < nb * W) o.table[i] = v;
     }
     for (int i = nb * W + tid; i < kTableRows * W; i += bs) o.table[i] = 0ull;
     for (int k = tid; k < r; k += bs) {

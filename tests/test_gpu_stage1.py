@@ -25,6 +25,19 @@ def _cases():
     for n in (1, 64, 100, 1024):
         c.append((f"zero{n}", np.zeros((n, n), dtype=np.uint8)))
         c.append((f"eye{n}", np.eye(n, dtype=np.uint8)))
+    for n in (192, 193, 250, 256, 257, 320):  # last one-warp widths (W <= 4), first CTA widths
+        c.append((f"sym{n}", synth.random_symmetric(n, 0.5, n)))
+    # pivots only among late rows: the first rows and columns are zero
+    for n, z in ((40, 33), (100, 50), (256, 200), (700, 600)):
+        A = synth.random_symmetric(n, 0.5, n + z)
+        A[:z, :] = 0
+        A[:, :z] = 0
+        c.append((f"late{n}-{z}", A))
+    # low rank: A = X X^T mod 2 with X of k columns
+    rng = np.random.default_rng(7)
+    for n, k in ((64, 5), (200, 17), (1024, 40)):
+        X = rng.integers(0, 2, size=(n, k), dtype=np.int64)
+        c.append((f"lowrank{n}-{k}", ((X @ X.T) & 1).astype(np.uint8)))
     c.append(("sparse300", synth.random_symmetric(300, 0.01, 3)))
     c.append(("dense1000", synth.random_symmetric(1000, 0.9, 4)))
     return c

@@ -215,9 +215,21 @@ def cpu_oracle_sample(target_s: float):
     F = oc.factor(A)
     oc.reduce(F, 0, 1 << k, cores)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, over a window sized for ~target_s / 4
+    t0 = time.perf_counter()
+    oc.reduce(F, 0, 1 << 20, 1)
+    rate1 = (1 << 20) / max(time.perf_counter() - t0, 1e-6)
+    k1 = 20
+    while k1 < F.r and (1 << (k1 + 1)) / rate1 <= target_s / 4:
+        k1 += 1
+    t0 = time.perf_counter()
+    oc.reduce(F, 0, 1 << k1, 1)
+    dt1 = time.perf_counter() - t0
     return {"value": (1 << k) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"oracle factor + reduce of solutions [0, 2^{k}) of the 2^{F.r} on {cores} threads "
-                      f"({dt:.1f} s)"}, k
+                      f"({dt:.1f} s)",
+            "single_thread": {"value": (1 << k1) / dt1, "unit": UNIT,
+                              "sample": f"oracle reduce of solutions [0, 2^{k1}) on 1 thread ({dt1:.1f} s)"}}, k
 
 
 def workload_config(r: int, reduce_n: int | None = None, store_n: int | None = None):

@@ -79,10 +79,15 @@ __device__ __forceinline__ void transpose64_warp(uint64_t& x0, uint64_t& x1, int
     }
 }
 
+// Row stride of the basis rows in shared memory: odd, so that 32 lanes reading
+// one word of 32 consecutive rows hit distinct banks.
+template <int W>
+constexpr int basis_stride() { return W | 1; }
+
 template <int W, int MAXN>
 constexpr size_t factor_smem_bytes(int n)
 {
-    return sizeof(FactorSmem<W, MAXN>) + (size_t)n * W * sizeof(uint64_t);
+    return sizeof(FactorSmem<W, MAXN>) + (size_t)n * basis_stride<W>() * sizeof(uint64_t);
 }
 
 // Factor the n x n matrix A ([n][W] words, global) with the whole CTA.
@@ -96,7 +101,8 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
 {
     constexpr int kNone = 0x7fffffff;
     FactorSmem<W, MAXN>& sm = *reinterpret_cast<FactorSmem<W, MAXN>*>(smem);
-    uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem + sizeof(FactorSmem<W, MAXN>));  // [n][W]
+    constexpr int SW = basis_stride<W>();
+    uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem + sizeof(FactorSmem<W, MAXN>));  // [n][SW]
 
     const int tid = threadIdx.x;
     const int bs = blockDim.x;
@@ -225,7 +231,7 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
         for (int j = 0; j < R; ++j) {
             if (!used[j]) continue;
 #pragma unroll
-            for (int v = 0; v < W; ++v) s_rows[my_k[j] * W + v] = row[j][v];
+            for (int v = 0; v < W; ++v) s_rows[my_k[j] * SW + v] = row[j][v];
         }
     }
     const int nb = r < HLF_MAX_VARYING ? r : HLF_MAX_VARYING;
@@ -233,7 +239,7 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
 
     // ---- outputs of step (1): B_k in pivot order, pivots, enumeration table
     for (int i = tid; i < r * W; i += bs) {
-        const uint64_t v = s_rows[i];
+        const uint64_t v = s_rows[(i / W) * SW + i % W];
         if (o.basis) o.basis[i] = v;
         if (i < nb * W) o.table[i] = v;
     }
@@ -253,10 +259,22 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
         const int fb = f & 63;
         if (lane < W) sm.x[warp][lane] = lane == fw ? (1ull << fb) : 0ull;
         __syncwarp();
-        for (int k = lane; k < r; k += 32) {
-            if ((s_rows[k * W + fw] >> fb) & 1ull) {
-                const int pc = sm.pivcol[k];
-                atomicOr(reinterpret_cast<unsigned long long*>(&sm.x[warp][pc >> 6]), 1ull << (pc & 63));
+        // bit p_k of x_f is B_k[f]. pivcol ascends with k, so the lanes of a
+        // 32-row chunk that set bits of one word of x_f are contiguous, and
+        // an OR over them sets that word.
+        for (int k0 = 0; k0 < r; k0 += 32) {
+            const int k = k0 + lane;
+            const bool has = k < r && ((s_rows[k * SW + fw] >> fb) & 1ull);
+            const int pc = has ? sm.pivcol[k] : 0;
+            unsigned pending = __ballot_sync(0xffffffffu, has);
+            while (pending) {  // one word of x_f per round (uniform)
+                const int wv = __shfl_sync(0xffffffffu, pc >> 6, __ffs(pending) - 1);
+                const bool mine = has && (pc >> 6) == wv;
+                const uint64_t bit = mine ? 1ull << (pc & 63) : 0ull;
+                const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)bit);
+                const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(bit >> 32));
+                if (lane == 0) sm.x[warp][wv] |= ((uint64_t)hi << 32) | lo;
+                pending &= ~__ballot_sync(0xffffffffu, mine);
             }
         }
         __syncwarp();

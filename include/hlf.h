@@ -151,6 +151,22 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
                                void* stream);
 
 /*
+ * Stage 2 for small instances, with no host round trip after hlf_factor
+ * (Section 2, Eq. 3): out_dev[i][0..W) = z(i) for i < min(2^r, cap), the same
+ * solutions in the same order as hlf_enumerate_store over that window. The
+ * kernel reads r on the device from the factorisation; nothing is written if
+ * the factorisation failed. The number written is min(2^r, cap) with r from
+ * hlf_get_rank, which returns at once once `stream` has been synchronised.
+ * Work on `stream` first waits for the factor kernel's stream.
+ * out_dev: device, caller-owned, cap * W uint64, 8-byte aligned. Requires
+ * cap <= HLF_STORE_UPTO_MAX (else HLF_ERR_ARG). Each solution is computed
+ * from its index with up to r row XORs, so large windows belong to
+ * hlf_enumerate_store.
+ */
+#define HLF_STORE_UPTO_MAX (1ull << 24)
+hlf_status hlf_enumerate_store_upto(hlf_handle* h, uint64_t cap, uint64_t* out_dev, void* stream);
+
+/*
  * Stage 2, materialised densely: the same solutions as hlf_enumerate_store,
  * n bits each, back to back. Solution z(offset + t) occupies bits
  * [t*n, (t+1)*n) of the stream at out_dev, where stream bit b is bit b % 64

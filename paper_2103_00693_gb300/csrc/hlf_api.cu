@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "hlf_internal.cuh"
+#include "upto.cuh"
 
 struct hlf_handle {
     int32_t n = 0;
@@ -27,7 +28,7 @@ struct hlf_handle {
     cudaStream_t use_stream[kMaxStreams] = {};
     cudaEvent_t use_event[kMaxStreams] = {};
     int n_uses = 0;
-    cudaStream_t priv = nullptr;     // private non-blocking stream for status reads
+    cudaStream_t priv = nullptr;     // private non-blocking stream, created on first need
     bool rank_known = false;
     int32_t r = -1;
 };
@@ -64,10 +65,38 @@ constexpr int kSlotWords = 16;
 constexpr int kSlotsPerSlab = 4096;
 std::mutex g_slot_mu;
 std::vector<int32_t*> g_free_slots;
+// Slots of destroyed handles whose last work may still be in flight, each with
+// an event recorded after that work (the event is owned here). Reclaimed in
+// order once the event has completed.
+struct PendingSlot {
+    int32_t* slot;
+    cudaEvent_t done;
+};
+std::vector<PendingSlot> g_pending_slots;
+size_t g_pending_head = 0;
+
+// Under g_slot_mu: recycle up to `max` pending slots whose work has finished.
+void reclaim_pending_slots(int max)
+{
+    while (max-- > 0 && g_pending_head < g_pending_slots.size()) {
+        PendingSlot& p = g_pending_slots[g_pending_head];
+        const cudaError_t q = cudaEventQuery(p.done);
+        if (q == cudaErrorNotReady) break;
+        cudaGetLastError();  // a failed query leaves the slot to be recycled as well
+        cudaEventDestroy(p.done);
+        g_free_slots.push_back(p.slot);
+        ++g_pending_head;
+    }
+    if (g_pending_head == g_pending_slots.size()) {
+        g_pending_slots.clear();
+        g_pending_head = 0;
+    }
+}
 
 int32_t* acquire_status_slot()
 {
     std::lock_guard<std::mutex> lock(g_slot_mu);
+    if (g_free_slots.empty()) reclaim_pending_slots(8);
     if (g_free_slots.empty()) {
         void* p = nullptr;
         if (cudaHostAlloc(&p, sizeof(int32_t) * kSlotWords * kSlotsPerSlab,
@@ -90,8 +119,22 @@ void release_status_slot(int32_t* slot)
     g_free_slots.push_back(slot);
 }
 
+// Recycle a slot once `done` (recorded after the last work that may write it)
+// has completed; takes ownership of the event.
+void defer_slot_release(int32_t* slot, cudaEvent_t done)
+{
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    g_pending_slots.push_back({slot, done});
+}
+
 // Host callback (no CUDA calls allowed in it): recycle a status slot.
 void CUDART_CB release_slot_cb(void* slot) { release_status_slot(static_cast<int32_t*>(slot)); }
+
+hlf_status ensure_priv(hlf_handle* h)
+{
+    if (h->priv) return HLF_OK;
+    return cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking) == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+}
 
 // Host wait for every stream's latest work through h.
 hlf_status wait_uses(hlf_handle* h)
@@ -276,8 +319,7 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
     h->table = reinterpret_cast<uint64_t*>(h->dmem + off_table);
     h->ptable = reinterpret_cast<uint64_t*>(h->dmem + off_ptable);
     h->basis = reinterpret_cast<uint64_t*>(h->dmem + off_basis);
-    if (cudaEventCreateWithFlags(&h->factored, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&h->factored, cudaEventDisableTiming) != cudaSuccess) {
         hlf_destroy(h);
         return HLF_ERR_CUDA;
     }
@@ -325,6 +367,7 @@ hlf_status hlf_get_factor(hlf_handle* h, int32_t* piv_host, uint64_t* z0_host, u
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
     hlf_status st = ensure_rank(h);
+    if (st == HLF_OK) st = ensure_priv(h);
     if (st != HLF_OK) return st;
     const size_t W = h->W;
     if (piv_host && h->r > 0 &&
@@ -364,6 +407,18 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
     if (count == 0) return HLF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return after_launch(h, hlf::launch_store(enum_table(h), h->W, offset, count, out_dev, s), s);
+}
+
+hlf_status hlf_enumerate_store_upto(hlf_handle* h, uint64_t cap, uint64_t* out_dev, void* stream)
+{
+    if (!h || (!out_dev && cap) || cap > HLF_STORE_UPTO_MAX) return HLF_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(out_dev) % 8) return HLF_ERR_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return HLF_ERR_CUDA;
+    if (cap == 0) return HLF_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamWaitEvent(s, h->factored, 0) != cudaSuccess) return HLF_ERR_CUDA;
+    return after_launch(h, hlf::launch_store_upto(enum_table(h), h->W, h->info_dev, cap, out_dev, s), s);
 }
 
 hlf_status hlf_enumerate_store_dense(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev,
@@ -449,19 +504,36 @@ hlf_status hlf_destroy(hlf_handle* h)
         // Device memory is freed, and the status slot recycled, in stream
         // order after the latest work on every stream that used the handle:
         // the host does not wait and no device-wide synchronisation happens.
+        // Used on one stream: the memory is freed on that stream and the slot
+        // recycled once the stream's use event has completed. Otherwise a
+        // private stream waits for every use event and does both.
         DeviceGuard g(h->device);
-        bool queued = h->priv != nullptr;
-        for (int i = 0; queued && i < h->n_uses; ++i)
-            queued = cudaStreamWaitEvent(h->priv, h->use_event[i], 0) == cudaSuccess;
-        if (queued && h->dmem) queued = cudaFreeAsync(h->dmem, h->priv) == cudaSuccess;
-        if (queued && h->info) queued = cudaLaunchHostFunc(h->priv, release_slot_cb, h->info) == cudaSuccess;
+        bool queued = false;
+        if (h->n_uses == 1) {
+            queued = !h->dmem || cudaFreeAsync(h->dmem, h->use_stream[0]) == cudaSuccess;
+            if (queued) {
+                h->dmem = nullptr;
+                if (h->info) {
+                    defer_slot_release(h->info, h->use_event[0]);
+                    h->use_event[0] = nullptr;  // owned by the pending list now
+                    h->info = nullptr;
+                }
+            }
+        } else {
+            queued = ensure_priv(h) == HLF_OK;
+            for (int i = 0; queued && i < h->n_uses; ++i)
+                queued = cudaStreamWaitEvent(h->priv, h->use_event[i], 0) == cudaSuccess;
+            if (queued && h->dmem) queued = cudaFreeAsync(h->dmem, h->priv) == cudaSuccess;
+            if (queued && h->info) queued = cudaLaunchHostFunc(h->priv, release_slot_cb, h->info) == cudaSuccess;
+        }
         if (!queued) {  // error paths only: wait, then release synchronously
             cudaGetLastError();
             wait_uses(h);
             if (h->dmem && cudaFree(h->dmem) != cudaSuccess) st = HLF_ERR_CUDA;
             if (h->info) release_status_slot(h->info);
         }
-        for (int i = 0; i < h->n_uses; ++i) cudaEventDestroy(h->use_event[i]);
+        for (int i = 0; i < h->n_uses; ++i)
+            if (h->use_event[i]) cudaEventDestroy(h->use_event[i]);
         if (h->factored) cudaEventDestroy(h->factored);
         if (h->priv) cudaStreamDestroy(h->priv);
     }

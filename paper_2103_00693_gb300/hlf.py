@@ -47,6 +47,7 @@ SIGNATURES = {
     "hlf_set_order": (ctypes.c_int, [_vp, _i32]),
     "hlf_get_status": (ctypes.c_int, [_vp]),
     "hlf_enumerate_store": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
+    "hlf_enumerate_store_upto": (ctypes.c_int, [_vp, _u64, _vp, _vp]),
     "hlf_enumerate_store_dense": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_reduce": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_reduce_chunks": (ctypes.c_int, [_vp, _u64, _u64, _u64, _vp, _vp]),
@@ -107,6 +108,11 @@ def _stream_ptr(stream) -> int | None:
     import torch
 
     if stream is None:
+        # the raw pointer of the current stream, without building a Stream object
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        dev = getattr(torch._C, "_cuda_getDevice", None)
+        if raw is not None and dev is not None and torch.cuda.is_initialized():
+            return raw(dev()) or None
         stream = torch.cuda.current_stream()
     return stream.cuda_stream or None
 
@@ -211,6 +217,13 @@ def hlf_get_status(h: int) -> int:
 def hlf_enumerate_store(h: int, offset: int, count: int, out_dev, stream=None):
     _check(load().hlf_enumerate_store(h, offset, count, _ptr(out_dev) if out_dev is not None else None,
                                       _stream_ptr(stream)), "hlf_enumerate_store")
+
+
+def hlf_enumerate_store_upto(h: int, cap: int, out_dev, stream=None):
+    """Every solution z(i), i < min(2^r, cap), into out_dev [cap, W], with r
+    read on the device: no host wait after hlf_factor."""
+    _check(load().hlf_enumerate_store_upto(h, cap, _ptr(out_dev) if out_dev is not None else None,
+                                           _stream_ptr(stream)), "hlf_enumerate_store_upto")
 
 
 def hlf_enumerate_store_dense(h: int, offset: int, count: int, out_dev, stream=None):
@@ -355,6 +368,16 @@ class Factorization:
         if out is None:
             out = torch.empty((count, self.W), dtype=torch.int64, device="cuda")
         hlf_enumerate_store(self.h, offset, count, out, stream)
+        return out
+
+    def store_upto(self, cap: int, out=None, stream=None):
+        """Solutions [0, min(2^r, cap)) into out [cap, W] without a host wait
+        for r; the first min(2^r, cap) rows are valid once the stream is done."""
+        import torch
+
+        if out is None:
+            out = torch.empty((cap, self.W), dtype=torch.int64, device="cuda")
+        hlf_enumerate_store_upto(self.h, cap, out, stream)
         return out
 
     def store_dense(self, offset: int, count: int, out=None, stream=None):

@@ -69,6 +69,7 @@ def test_host_side_argument_checks(lib):
     r = ctypes.c_int32()
     assert lib.hlf_get_rank(None, ctypes.byref(r)) == 1
     assert lib.hlf_enumerate_store(None, 0, 1, fake, None) == 1
+    assert lib.hlf_enumerate_store_upto(None, 1, fake, None) == 1
     assert lib.hlf_enumerate_reduce(None, 0, 1, fake, None) == 1
     assert lib.hlf_sample(None, fake, 1, fake, None) == 1
     assert lib.hlf_get_status(None) == 1

@@ -1,0 +1,105 @@
+"""hlf_enumerate_store_upto (every solution of a small instance, the rank read
+on the device) against the oracle, bit-exact: the first min(2^r, cap) rows
+equal the oracle's window [0, min(2^r, cap)), the rest of the buffer is
+untouched, a failed factorisation writes nothing, and a second stream waits
+for the factor kernel."""
+
+import numpy as np
+import pytest
+
+import paper_2103_00693_gb300 as hlf
+import synth
+from oracle import cpu as oc
+
+pytestmark = pytest.mark.gpu
+
+SENTINEL = 0x5A5A5A5A5A5A5A5A
+
+
+def _cases():
+    c = [("grid3", synth.grid_instance(3, 0.5, 5)), ("grid4", synth.grid_instance(4, 1.0, 1)),
+         ("zero6", np.zeros((6, 6), dtype=np.uint8)), ("eye1", np.eye(1, dtype=np.uint8))]
+    for N, b in ((2, "0000"), (3, "101010101")):
+        c.append((f"paper{N}", synth.all_connected(N, b)))
+    c.append(("sym70", synth.random_symmetric(70, 0.03, 70)))  # W = 2, r = 58
+    c.append(("sym130", synth.random_symmetric(130, 0.01, 130)))  # W = 3, r = 82
+    return c
+
+
+def _run(A, cap, stream=None, order=None):
+    import torch
+
+    G = hlf.Factorization.from_dense(A)
+    try:
+        if order is not None:
+            G.set_order(order)
+        out = torch.full((max(cap, 1), G.W), SENTINEL, dtype=torch.int64, device="cuda")
+        hlf.hlf_enumerate_store_upto(G.h, cap, out, stream)
+        torch.cuda.synchronize()
+        return oc.factor(A), G.rank, out.cpu().numpy().view(np.uint64)
+    finally:
+        G.close()
+
+
+@pytest.mark.parametrize("name,A", _cases(), ids=[c[0] for c in _cases()])
+def test_upto_all_solutions(cuda_ok, name, A):
+    F = oc.factor(A)
+    space = 1 << min(F.r, 16)  # all solutions up to r = 16, a prefix above
+    for cap in sorted({1, 3, min(space, 64), space, space + 5}):
+        F, r, got = _run(A, cap)
+        cnt = min(1 << r, cap)
+        assert np.array_equal(got[:cnt], oc.window(F, 0, cnt)), (name, cap)
+        assert (got[cnt:] == np.uint64(SENTINEL)).all(), (name, cap)
+
+
+def test_upto_paper_order(cuda_ok):
+    A = synth.all_connected(3, "101010101")
+    F, r, got = _run(A, 1 << 9, order=hlf.ORDER_PAPER)
+    assert np.array_equal(got[:1 << r], oc.paper_order(F, 0, 1 << r))
+
+
+def test_upto_failed_factor_writes_nothing(cuda_ok):
+    import torch
+
+    A = np.zeros((8, 8), dtype=np.uint8)
+    A[0, 1] = 1  # not symmetric
+    G = hlf.Factorization.from_dense(A)
+    try:
+        out = torch.full((16, 1), SENTINEL, dtype=torch.int64, device="cuda")
+        hlf.hlf_enumerate_store_upto(G.h, 16, out)
+        torch.cuda.synchronize()
+        assert (out.cpu().numpy().view(np.uint64) == np.uint64(SENTINEL)).all()
+        assert G.status() == 3  # HLF_ERR_NOT_SYMMETRIC
+    finally:
+        G.close()
+
+
+def test_upto_other_stream_waits_for_factor(cuda_ok):
+    import torch
+
+    A = synth.grid_instance(32, 0.5, 9)  # n = 1024: a factor kernel long enough to race
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    try:
+        s = torch.cuda.Stream()
+        out = torch.zeros((1 << 12, G.W), dtype=torch.int64, device="cuda")
+        hlf.hlf_enumerate_store_upto(G.h, 1 << 12, out, s)
+        s.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), oc.window(F, 0, 1 << 12))
+    finally:
+        G.close()
+
+
+def test_upto_argument_checks(cuda_ok):
+    import torch
+
+    A = synth.grid_instance(3, 0.5, 5)
+    G = hlf.Factorization.from_dense(A)
+    try:
+        out = torch.empty((4, 1), dtype=torch.int64, device="cuda")
+        with pytest.raises(hlf.HlfError) as e:
+            hlf.hlf_enumerate_store_upto(G.h, (1 << 24) + 1, out)
+        assert e.value.status == 1
+        hlf.hlf_enumerate_store_upto(G.h, 0, None)  # nothing to do
+    finally:
+        G.close()

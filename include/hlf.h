@@ -222,8 +222,10 @@ hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64
 
 /* Frees the handle. Its device buffers (allocated stream-ordered on the
  * stream given to hlf_factor) are released in stream order after the last
- * work enqueued through the handle; the host does not wait. NULL is
- * accepted. */
+ * work enqueued through the handle; the host does not wait. If every call
+ * used one stream, the release is enqueued on that stream (a free, which
+ * delays nothing that follows); otherwise on a private stream that waits for
+ * each stream's last use. NULL is accepted. */
 hlf_status hlf_destroy(hlf_handle* h);
 
 /* ------------------------------------------------------------ many windows

@@ -90,6 +90,9 @@ void reclaim_pending_slots(int max)
     if (g_pending_head == g_pending_slots.size()) {
         g_pending_slots.clear();
         g_pending_head = 0;
+    } else if (g_pending_head >= 1024 && 2 * g_pending_head >= g_pending_slots.size()) {
+        g_pending_slots.erase(g_pending_slots.begin(), g_pending_slots.begin() + (long)g_pending_head);
+        g_pending_head = 0;  // the list never outgrows twice its live entries
     }
 }
 

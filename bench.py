@@ -484,6 +484,7 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
 
     for _ in range(max(1, args.warmup)):
         step()
+    link = d2h_gbs(out_host, out, copy_stream)
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -497,7 +498,26 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
     h2d = A_host.numel() * 8 + idx_pin.numel() * 8
     d2h = out_host.numel() * 8 + smp_host.numel() * 8 + red_host.numel() * 8
     return {"value": world * args.steps * total / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / args.steps}
+            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / args.steps,
+            "d2h_gbs": link}
+
+
+def d2h_gbs(dst_host, src_dev, stream) -> float:
+    """Device-to-host bandwidth into this pinned buffer right now (best of two
+    copies, CUDA events): the host link is shared with the machine's other
+    jobs, so the e2e and served figures are read against it."""
+    import torch
+
+    best = 0.0
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record()
+            dst_host.copy_(src_dev, non_blocking=True)
+            e1.record()
+        e1.synchronize()
+        best = max(best, src_dev.numel() * src_dev.element_size() / (e0.elapsed_time(e1) * 1e6))
+    return best
 
 
 def run_configs(dev):
@@ -626,10 +646,16 @@ def run_served(args):
     from synth import workloads as wl
 
     out = {"workload": "Poisson stream, N uniform 3..32 (n <= 1024), p=1/2, windows 2^10..2^24 to host"}
+    import torch
+
     warm = wl.stream(8, 1000.0, seed=1)
     srv = serve.Server(keep_results=False)
     srv.run(warm)
     serve.run_plain(warm, keep_results=False)
+    words = (1 << 30) // 8
+    src = torch.empty(words, dtype=torch.int64, device="cuda")
+    out["host_ring_d2h_gbs"] = d2h_gbs(srv.host_ring.buf[:words], src, torch.cuda.Stream())
+    del src
     for name, rate, count in (("low_load", 50.0, 60), ("high_load", 2000.0, 200), ("overload", 5000.0, 300)):
         reqs = wl.stream(count, rate)
         st, _ = srv.run(reqs)

@@ -224,7 +224,7 @@ hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64
  * stream given to hlf_factor) are released in stream order after the last
  * work enqueued through the handle; the host does not wait. If every call
  * used one stream, the release is enqueued on that stream (a free, which
- * delays nothing that follows); otherwise on a private stream that waits for
+ * delays nothing that follows); otherwise on a library stream that waits for
  * each stream's last use. NULL is accepted. */
 hlf_status hlf_destroy(hlf_handle* h);
 

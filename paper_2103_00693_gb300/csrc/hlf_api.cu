@@ -130,8 +130,21 @@ void defer_slot_release(int32_t* slot, cudaEvent_t done)
     g_pending_slots.push_back({slot, done});
 }
 
-// Host callback (no CUDA calls allowed in it): recycle a status slot.
-void CUDART_CB release_slot_cb(void* slot) { release_status_slot(static_cast<int32_t*>(slot)); }
+// One non-blocking stream per device, created on first need, on which
+// hlf_destroy of a handle used on several streams waits for each stream's
+// last use and then frees. Nothing on the host ever waits on it.
+cudaStream_t release_stream(int dev)
+{
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
 
 hlf_status ensure_priv(hlf_handle* h)
 {
@@ -508,8 +521,9 @@ hlf_status hlf_destroy(hlf_handle* h)
         // order after the latest work on every stream that used the handle:
         // the host does not wait and no device-wide synchronisation happens.
         // Used on one stream: the memory is freed on that stream and the slot
-        // recycled once the stream's use event has completed. Otherwise a
-        // private stream waits for every use event and does both.
+        // recycled once the stream's use event has completed. Otherwise the
+        // device's release stream waits for every use event, frees, and
+        // records the event that recycles the slot.
         DeviceGuard g(h->device);
         bool queued = false;
         if (h->n_uses == 1) {
@@ -523,11 +537,23 @@ hlf_status hlf_destroy(hlf_handle* h)
                 }
             }
         } else {
-            queued = ensure_priv(h) == HLF_OK;
+            cudaStream_t rs = release_stream(h->device);
+            queued = rs != nullptr;
             for (int i = 0; queued && i < h->n_uses; ++i)
-                queued = cudaStreamWaitEvent(h->priv, h->use_event[i], 0) == cudaSuccess;
-            if (queued && h->dmem) queued = cudaFreeAsync(h->dmem, h->priv) == cudaSuccess;
-            if (queued && h->info) queued = cudaLaunchHostFunc(h->priv, release_slot_cb, h->info) == cudaSuccess;
+                queued = cudaStreamWaitEvent(rs, h->use_event[i], 0) == cudaSuccess;
+            if (queued && h->dmem) queued = cudaFreeAsync(h->dmem, rs) == cudaSuccess;
+            if (queued) h->dmem = nullptr;
+            if (queued && h->info) {
+                cudaEvent_t done = nullptr;
+                queued = cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess &&
+                         cudaEventRecord(done, rs) == cudaSuccess;
+                if (queued) {
+                    defer_slot_release(h->info, done);
+                    h->info = nullptr;
+                } else if (done) {
+                    cudaEventDestroy(done);
+                }
+            }
         }
         if (!queued) {  // error paths only: wait, then release synchronously
             cudaGetLastError();

@@ -132,6 +132,7 @@ class Req:
     A_dev: object = None
     ev_factor: object = None
     ev_copy: object = None
+    lane: int = 0  # which factor stream
 
 
 @dataclass
@@ -237,7 +238,8 @@ class Server:
         q.blk_dev, q.blk_host, q.blk_in, q.blk_mat = bd, bh, bi, bm
         staged = self.in_ring.view(bi, q.n * q.W)
         staged.copy_(torch.from_numpy(hlf.pack_rows(q.A).view(np.int64).ravel()))
-        sf = self.s_factors[self._next_factor]
+        q.lane = self._next_factor
+        sf = self.s_factors[q.lane]
         self._next_factor = (self._next_factor + 1) % len(self.s_factors)
         with torch.cuda.stream(sf):
             q.A_dev = self.mat_ring.view(bm, q.n * q.W).view(q.n, q.W)
@@ -256,26 +258,31 @@ class Server:
 
         reqs = _mk_reqs(stream)
         waiting = collections.deque(reqs)
-        factoring: list[Req] = []
+        # one FIFO per factor stream: a stream's factor kernels finish in
+        # order, so only each queue's head needs an event query
+        factoring = [collections.deque() for _ in self.s_factors]
         copying: list[Req] = []
         done: list[Req] = []
         st = Stats(n_requests=len(reqs))
         t0 = time.perf_counter()
         busy_since = None
-        while waiting or factoring or copying:
+        while waiting or any(factoring) or copying:
             now = time.perf_counter() - t0
             while waiting and waiting[0].t_arrival <= now:
                 if not self._admit(waiting[0]):
-                    if not (factoring or copying):
+                    if not (any(factoring) or copying):
                         raise RuntimeError(f"request {waiting[0].id} does not fit the rings")
                     break
-                factoring.append(waiting.popleft())
+                q = waiting.popleft()
+                factoring[q.lane].append(q)
                 if busy_since is None:
                     busy_since = now
-            ready = [q for q in factoring if q.ev_factor.query()][: self.max_batch]
+            ready = []
+            for fq in factoring:
+                while fq and len(ready) < self.max_batch and fq[0].ev_factor.query():
+                    ready.append(fq.popleft())
             if ready:
                 for q in ready:
-                    factoring.remove(q)
                     self.in_ring.free(q.blk_in)
                     q.r = hlf.hlf_get_rank(q.h)
                     q.offset, q.count = window_of(q.r, q.want, q.u)
@@ -313,11 +320,11 @@ class Server:
                 self.dev_ring.free(q.blk_dev)
                 self.host_ring.free(q.blk_host)
                 done.append(q)
-            if busy_since is not None and not (factoring or copying):
+            if busy_since is not None and not (any(factoring) or copying):
                 st.busy_s += (time.perf_counter() - t0) - busy_since
                 busy_since = None
             if not ready and not finished:
-                if waiting and not factoring and not copying:
+                if waiting and not any(factoring) and not copying:
                     dt = waiting[0].t_arrival - (time.perf_counter() - t0)
                     if dt > 0:
                         time.sleep(min(dt, 0.001))

@@ -301,11 +301,11 @@ __device__ __forceinline__ void dense2_put(uint64_t* st, const uint64_t (&z)[W],
 // plainly, then the odd ones merge into the first and last words they share.
 // The group's words leave in one bulk store when the output is 16-byte aligned
 // and n is even (n*8 bytes, a multiple of 16), else the warp copies them out.
-template <int W, bool Bulk>
+template <int W, bool Bulk, int P>
 __global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __restrict__ table, Dense2Plan pl,
                                                             uint64_t* __restrict__ out)
 {
-    extern __shared__ __align__(16) uint64_t s_stage2[];  // [warps][nbuf][n]
+    extern __shared__ __align__(16) uint64_t s_stage2[];  // [warps][nbuf][P * n]
     __shared__ Table<W> t;
     __shared__ uint64_t s_C[kD2Steps][W];
     load_table<W>(t, table);
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __re
     if (k0 >= pl.groups) return;
     const uint64_t k1 = min(k0 + pl.per_warp, pl.groups);
     const int n = pl.n;
-    uint64_t* const stages = s_stage2 + (size_t)warp * pl.nbuf * n;
+    uint64_t* const stages = s_stage2 + (size_t)warp * pl.nbuf * P * n;
 
     const uint32_t tA = 2 * lane, tB = 2 * lane + 1;  // this lane's solutions in every group
     const int bA = (int)((tA * n) >> 6), bB = (int)((tB * n) >> 6);
@@ -338,8 +338,9 @@ __global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __re
     seed<W>(t, iA, zA);
     seed<W>(t, iA + 1, zB);
 
+    // P consecutive groups share a staging buffer and leave in one store
     for (uint64_t k = k0;;) {
-        uint64_t* st = stages + (size_t)((k - k0) & (uint64_t)(pl.nbuf - 1)) * n;
+        uint64_t* st = stages + (size_t)(((k - k0) / P) & (uint64_t)(pl.nbuf - 1)) * P * n;
         if constexpr (Bulk) {  // the bulk store that last read this buffer is done reading it
             if (lane == 0) {
                 if (pl.nbuf == 2) bulk_wait_read<1>();
@@ -347,37 +348,47 @@ __global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __re
             }
             __syncwarp();
         }
-        if (k < pl.full) {
-            dense2_put<W, false>(st + bA, zA, true, cA, LA, false, false);
-            __syncwarp();
-            dense2_put<W, false>(st + bB, zB, true, cB, LB, mfB, mlB);
-        } else {
-            const uint64_t rem = pl.count - 64 * k;
-            dense2_put<W, true>(st + bA, zA, tA < rem, cA, LA, false, false);
-            __syncwarp();
-            dense2_put<W, true>(st + bB, zB, tB < rem, cB, LB, mfB, mlB);
+        const int pg = (int)min((uint64_t)P, k1 - k);  // groups in this step (uniform)
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (p < pg) {
+                uint64_t* sg = st + p * n;
+                const uint64_t kk = k + p;
+                if (kk < pl.full) {
+                    dense2_put<W, false>(sg + bA, zA, true, cA, LA, false, false);
+                    __syncwarp();
+                    dense2_put<W, false>(sg + bB, zB, true, cB, LB, mfB, mlB);
+                } else {
+                    const uint64_t rem = pl.count - 64 * kk;
+                    dense2_put<W, true>(sg + bA, zA, tA < rem, cA, LA, false, false);
+                    __syncwarp();
+                    dense2_put<W, true>(sg + bB, zB, tB < rem, cB, LB, mfB, mlB);
+                }
+                if (kk + 1 < k1) {  // on to group kk + 1
+                    HA += 1;  // H < 2^58, so ctz(H + 1) <= 58
+                    xor_row<W>(zA, s_C[ctz64(HA)]);
+                    HB += 1;
+                    xor_row<W>(zB, s_C[ctz64(HB)]);
+                }
+            }
         }
         const uint64_t w0 = k * (uint64_t)n;
-        const int nw = (int)min((uint64_t)n, pl.words - w0);
-        if (Bulk && nw == n) {
+        const int nw = (int)min((uint64_t)pg * n, pl.words - w0);
+        if (Bulk && nw == P * n) {
             fence_smem_to_async_proxy();
             __syncwarp();
-            if (lane == 0) bulk_store(out + w0, st, (uint32_t)(n * sizeof(uint64_t)));
+            if (lane == 0) bulk_store(out + w0, st, (uint32_t)(P * n * sizeof(uint64_t)));
         } else {
             __syncwarp();
             for (int q = lane; q < nw; q += 32) st_cs(out + w0 + q, st[q]);
             __syncwarp();
         }
-        if (++k == k1) break;
-        HA += 1;  // H < 2^58, so ctz(H + 1) <= 58
-        xor_row<W>(zA, s_C[ctz64(HA)]);
-        HB += 1;
-        xor_row<W>(zB, s_C[ctz64(HB)]);
+        k += (uint64_t)pg;
+        if (k == k1) break;
     }
     if (Bulk && lane == 0) bulk_wait_all();
 }
-
-template <int W, bool Bulk>
+template <int W, bool Bulk, int P>
 hlf_status launch_dense2_k(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
                            cudaStream_t s)
 {
@@ -388,38 +399,44 @@ hlf_status launch_dense2_k(const uint64_t* table, int n, uint64_t offset, uint64
     pl.full = count / 64;
     pl.groups = pl.full + (count % 64 != 0);
     pl.words = (count * (uint64_t)n + 63) / 64;  // count * n <= 2^64 - 64 (checked by the caller)
-    pl.nbuf = (Bulk && n <= 512) ? 2 : 1;
-    const size_t smem = (size_t)kD2Warps * pl.nbuf * n * sizeof(uint64_t);  // <= 64 KB
+    pl.nbuf = (Bulk && P * n <= 512) ? 2 : 1;
+    const size_t smem = (size_t)kD2Warps * pl.nbuf * P * n * sizeof(uint64_t);  // <= 64 KB
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(dense2_kernel<W, Bulk>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(dense2_kernel<W, Bulk, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kD2Warps * 1024 * (int)sizeof(uint64_t)) != cudaSuccess)
             return HLF_ERR_CUDA;
         attr_set[dev] = true;
     }
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense2_kernel<W, Bulk>, kD2Threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense2_kernel<W, Bulk, P>, kD2Threads, smem) !=
         cudaSuccess)
         return HLF_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
     const uint64_t max_warps = (uint64_t)sm_count() * per_sm * kD2Warps;
     const uint64_t warps = pl.groups < max_warps ? pl.groups : max_warps;
     pl.per_warp = (pl.groups + warps - 1) / warps;
+    pl.per_warp = (pl.per_warp + P - 1) / P * P;  // whole steps of P groups
     const uint64_t used = (pl.groups + pl.per_warp - 1) / pl.per_warp;
     const unsigned blocks = (unsigned)((used + kD2Warps - 1) / kD2Warps);
-    dense2_kernel<W, Bulk><<<blocks, kD2Threads, smem, s>>>(table, pl, out);
+    dense2_kernel<W, Bulk, P><<<blocks, kD2Threads, smem, s>>>(table, pl, out);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
+// Rows of up to four words (n <= 256) place two groups per staging buffer and
+// store them together: the per-group handshake and store are then shared by
+// four solutions per lane, and 2n words are a whole number of 16-byte units
+// for odd n as well.
 template <int W>
 hlf_status launch_dense2(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
                          cudaStream_t s)
 {
-    if (reinterpret_cast<uintptr_t>(out) % 16 == 0 && n % 2 == 0)
-        return launch_dense2_k<W, true>(table, n, offset, count, out, s);
-    return launch_dense2_k<W, false>(table, n, offset, count, out, s);
+    constexpr int P = W <= 4 ? 2 : 1;
+    if (reinterpret_cast<uintptr_t>(out) % 16 == 0 && (P == 2 || n % 2 == 0))
+        return launch_dense2_k<W, true, P>(table, n, offset, count, out, s);
+    return launch_dense2_k<W, false, P>(table, n, offset, count, out, s);
 }
 
 }  // namespace

@@ -24,8 +24,9 @@
 // takes the 8-byte aligned outputs this entry point allows).
 //
 // n > 64, dense2_kernel: 64 solutions of n bits are exactly n words, so a
-// warp produces one such group per step, two solutions per lane, each placed
-// with funnel shifts at its bit offset in the group (see dense2_kernel).
+// warp produces one such group per step (two for n <= 256), two solutions per
+// lane, each placed with funnel shifts at its bit offset in the group (see
+// dense2_kernel).
 
 #include "enum_impl.cuh"
 
@@ -299,8 +300,9 @@ __device__ __forceinline__ void dense2_put(uint64_t* st, const uint64_t (&z)[W],
 // W or W+1 words. As n > 64, a word holds bits of at most two solutions, and
 // solutions t and t+2 share none: the even solutions place their words first,
 // plainly, then the odd ones merge into the first and last words they share.
-// The group's words leave in one bulk store when the output is 16-byte aligned
-// and n is even (n*8 bytes, a multiple of 16), else the warp copies them out.
+// P consecutive groups (P = 2 for n <= 256) share a staging buffer. Their P*n
+// words leave in one bulk store when the output is 16-byte aligned and P*n*8
+// bytes is a multiple of 16 (n even, or P = 2), else the warp copies them out.
 template <int W, bool Bulk, int P>
 __global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __restrict__ table, Dense2Plan pl,
                                                             uint64_t* __restrict__ out)

@@ -141,7 +141,7 @@ class ClockSampler:
         self.file.seek(0)
         rows = [ln.split(",") for ln in self.file.read().strip().splitlines() if ln.strip()]
         os.unlink(self.file.name)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             if len(r) < 9:
@@ -151,13 +151,20 @@ class ClockSampler:
                 mx.append(float(r[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(r[3]))
+            except ValueError:
+                pass
             for name, v in zip(names, r[5:9]):
                 if v.strip().lower() == "active":
                     reasons.add(name)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if pw:
+            out["power_w"] = statistics.median(pw)
+        return out
 
 
 def dist_setup(args):
@@ -485,6 +492,8 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
     for _ in range(max(1, args.warmup)):
         step()
     link = d2h_gbs(out_host, out, copy_stream)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -493,13 +502,14 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
     torch.cuda.synchronize(dev)
     dt = max_over_ranks(time.perf_counter() - t0, world)
     barrier(world)
+    clk = clocks.stop()
     if int(red_host[0]) != total:
         raise RuntimeError("e2e reduce count mismatch")
     h2d = A_host.numel() * 8 + idx_pin.numel() * 8
     d2h = out_host.numel() * 8 + smp_host.numel() * 8 + red_host.numel() * 8
     return {"value": world * args.steps * total / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt / args.steps,
-            "d2h_gbs": link}
+            "d2h_gbs": link, "clocks": clk}
 
 
 def d2h_gbs(dst_host, src_dev, stream) -> float:
@@ -656,11 +666,14 @@ def run_served(args):
     src = torch.empty(words, dtype=torch.int64, device="cuda")
     out["host_ring_d2h_gbs"] = d2h_gbs(srv.host_ring.buf[:words], src, torch.cuda.Stream())
     del src
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for name, rate, count in (("low_load", 50.0, 60), ("high_load", 2000.0, 200), ("overload", 5000.0, 300)):
         reqs = wl.stream(count, rate)
         st, _ = srv.run(reqs)
         pl, _ = serve.run_plain(reqs, keep_results=False)
         out[name] = {"rate_per_s": rate, "requests": count, "batched": st.summary(), "plain": pl.summary()}
+    out["clocks"] = clocks.stop()
     srv.close()
     return out
 

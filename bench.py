@@ -514,8 +514,8 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
 
 def d2h_gbs(dst_host, src_dev, stream) -> float:
     """Device-to-host bandwidth into this pinned buffer right now (best of two
-    copies, CUDA events): the host link is shared with the machine's other
-    jobs, so the e2e and served figures are read against it."""
+    copies, CUDA events). It varies with the state of the host, so the e2e and
+    served figures are read against it."""
     import torch
 
     best = 0.0

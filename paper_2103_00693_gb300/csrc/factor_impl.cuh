@@ -267,7 +267,7 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
             const bool has = k < r && ((s_rows[k * SW + fw] >> fb) & 1ull);
             const int pc = has ? sm.pivcol[k] : 0;
             unsigned pending = __ballot_sync(0xffffffffu, has);
-            while (pending) {  // one word of x_f per round (uniform)
+            while (pending) {  // one word of x_f per pass (uniform)
                 const int wv = __shfl_sync(0xffffffffu, pc >> 6, __ffs(pending) - 1);
                 const bool mine = has && (pc >> 6) == wv;
                 const uint64_t bit = mine ? 1ull << (pc & 63) : 0ull;

@@ -387,16 +387,28 @@ def run_hlf(args, world, rank, local):
             "gpu_launches": 4 * args.steps,
             "clocks": clk}
 
+    # The e2e leg's pinned host buffers and the serving rings are pinned now,
+    # after the timed step and well before their own legs: on a box that has
+    # done much GPU work, host transfers and launches right after pinning
+    # gigabytes of host memory were measured to run slow for a while.
+    e2e_host = None if args.no_e2e else {
+        "out": torch.empty((store_n, W), dtype=torch.int64, pin_memory=True),
+        "smp": torch.empty((m, W), dtype=torch.int64, pin_memory=True),
+        "red": torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, pin_memory=True)}
+    server = None
+    if not args.no_served:
+        from paper_2103_00693_gb300 import serve
+        server = serve.Server(keep_results=False)
     line["next_rows"] = run_next_rows(args, A_dev, n, W, store_n, pk, dev)
     line["configs"] = run_configs(dev)
     if not args.no_e2e:
-        line["e2e"] = run_e2e(args, world, dev, A, r, total, store_n, idx_host)
+        line["e2e"] = run_e2e(args, world, dev, A, r, total, store_n, idx_host, e2e_host)
     del out, smp
     torch.cuda.empty_cache()
     if not args.no_batched:
         line["batched"] = run_batched(args)
     if not args.no_served:
-        line["served"] = run_served(args)
+        line["served"] = run_served(args, server)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], _ = cpu_oracle_sample(args.cpu_seconds)
     if rank == 0:
@@ -442,7 +454,7 @@ def run_next_rows(args, A_dev, n, W, store_n, pk, dev):
                           "solutions_per_s": hcount / (h_ms / 1e3)}}
 
 
-def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
+def run_e2e(args, world, dev, A, r, total, store_n, idx_host, host_bufs=None):
     """The same step through the C ABI from host buffers: A and the sample
     indices are copied in from pinned memory, the 2^30 stored solutions, the
     samples and the reduce result are copied back, all inside the timed
@@ -462,9 +474,11 @@ def run_e2e(args, world, dev, A, r, total, store_n, idx_host):
     out = torch.empty((store_n, W), dtype=torch.int64, device=dev)
     smp = torch.empty((m, W), dtype=torch.int64, device=dev)
     red = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, device=dev)
-    out_host = torch.empty((store_n, W), dtype=torch.int64, pin_memory=True)
-    smp_host = torch.empty((m, W), dtype=torch.int64, pin_memory=True)
-    red_host = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, pin_memory=True)
+    if host_bufs is None:
+        host_bufs = {"out": torch.empty((store_n, W), dtype=torch.int64, pin_memory=True),
+                     "smp": torch.empty((m, W), dtype=torch.int64, pin_memory=True),
+                     "red": torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, pin_memory=True)}
+    out_host, smp_host, red_host = host_bufs["out"], host_bufs["smp"], host_bufs["red"]
     stream = torch.cuda.current_stream(dev)
 
     copy_stream = torch.cuda.Stream(dev)
@@ -647,7 +661,7 @@ def run_batched(args):
             "speedup_vs_plain": plain_s / (ms / 1e3)}
 
 
-def run_served(args):
+def run_served(args, srv=None):
     """The served workload: Poisson arrivals, N uniform 3..32, windows
     log-uniform 2^10..2^24 solutions returned to pinned host memory. The
     continuous-batching server and the plain one-request-at-a-time path see
@@ -659,7 +673,8 @@ def run_served(args):
     import torch
 
     warm = wl.stream(8, 1000.0, seed=1)
-    srv = serve.Server(keep_results=False)
+    if srv is None:
+        srv = serve.Server(keep_results=False)
     srv.run(warm)
     serve.run_plain(warm, keep_results=False)
     words = (1 << 30) // 8

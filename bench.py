@@ -325,6 +325,9 @@ def run_hlf(args, world, rank, local):
     def step(evs=None):
         hh = hlf.hlf_factor(A_dev, n, stream)
         if evs:
+            # the reduce needs r on the host: wait for it before the start
+            # event, so that the event brackets the reduce kernel alone
+            hlf.hlf_get_rank(hh)
             evs[0].record(stream)
         hlf.hlf_enumerate_reduce(hh, 0, total, red, stream)
         if evs:

@@ -71,6 +71,44 @@ def test_factor_rejects_non_symmetric(cuda_ok):
     G.close()
 
 
+ASYM = [(64, 0, 63), (64, 40, 7), (100, 99, 64), (100, 64, 99), (100, 70, 10),
+        (1000, 0, 999), (1000, 999, 0), (1000, 500, 501), (1000, 37, 485), (1000, 63, 64),
+        (1000, 960, 999), (1000, 33, 2), (1024, 1023, 1022), (1024, 96, 1000)]
+
+
+@pytest.mark.parametrize("n,i,j", ASYM, ids=[f"n{n}-{i}-{j}" for n, i, j in ASYM])
+def test_factor_finds_one_asymmetric_bit(cuda_ok, n, i, j):
+    """A single flipped bit A[i][j] (i != j) is found wherever it lies: in a
+    diagonal or off-diagonal 64 x 64 block, above or below the diagonal, in
+    either half of a block's rows, next to the padding."""
+    A = synth.random_symmetric(n, 0.3, n + i)
+    A[i, j] ^= 1
+    G = hlf.Factorization.from_dense(A)
+    try:
+        with pytest.raises(hlf.HlfError) as e:
+            G.rank
+        assert e.value.status == 3
+    finally:
+        G.close()
+
+
+def test_factor_padding_wins_over_asymmetry(cuda_ok):
+    import torch
+
+    n = 1000
+    A = synth.random_symmetric(n, 0.3, 11)
+    A[5, 900] ^= 1  # not symmetric
+    packed = hlf.pack_rows(A)
+    packed[999, 15] |= np.uint64(1) << np.uint64(63)  # and a padding bit (column 1023)
+    h = hlf.hlf_factor(torch.from_numpy(packed.view(np.int64)).cuda(), n)
+    try:
+        with pytest.raises(hlf.HlfError) as e:
+            hlf.hlf_get_rank(h)
+        assert e.value.status == 4
+    finally:
+        hlf.hlf_destroy(h)
+
+
 def test_factor_rejects_padding_bits(cuda_ok):
     import torch
 

@@ -23,6 +23,9 @@ def _cases():
         c.append((f"paper{N}", synth.all_connected(N, b)))
     c.append(("sym70", synth.random_symmetric(70, 0.03, 70)))  # W = 2, r = 58
     c.append(("sym130", synth.random_symmetric(130, 0.01, 130)))  # W = 3, r = 82
+    rng = np.random.default_rng(3)
+    X = rng.integers(0, 2, size=(1000, 10), dtype=np.int64)
+    c.append(("lowrank1000", ((X @ X.T) & 1).astype(np.uint8)))  # W = 16, every solution
     return c
 
 
@@ -103,3 +106,29 @@ def test_upto_argument_checks(cuda_ok):
         hlf.hlf_enumerate_store_upto(G.h, 0, None)  # nothing to do
     finally:
         G.close()
+
+
+def test_many_handles_recycle_status_slots(cuda_ok):
+    """More handles than one slab of status slots (4096), created and
+    destroyed in turn, half of them used on a second stream: every rank and
+    every stored block stays right while slots are recycled."""
+    import torch
+
+    A = synth.grid_instance(3, 0.5, 5)
+    F = oc.factor(A)
+    want = oc.window(F, 0, 1 << F.r)
+    A_dev = torch.from_numpy(hlf.pack_rows(A).view(np.int64)).cuda()
+    side = torch.cuda.Stream()
+    out = torch.empty((1 << 9, 1), dtype=torch.int64, device="cuda")
+    for k in range(4500):
+        h = hlf.hlf_factor(A_dev, 9)
+        if k % 2:
+            hlf.hlf_enumerate_store_upto(h, 1 << 9, out, side)
+            side.synchronize()
+        else:
+            hlf.hlf_enumerate_store_upto(h, 1 << 9, out)
+            torch.cuda.synchronize()
+        assert hlf.hlf_get_rank(h) == F.r
+        if k % 500 == 0:
+            assert np.array_equal(out[:1 << F.r].cpu().numpy().view(np.uint64), want)
+        hlf.hlf_destroy(h)

@@ -9,9 +9,9 @@
 //       minimum also names the warp that holds row p. Each warp stages its
 //       lowest candidate's words next to its key, so one barrier per column
 //       suffices: after it every thread knows p and reads row p from that
-//       warp's slot, and every other
-//       row with bit c set XORs it in (rows above and below: Gauss-Jordan, so
-//       the result is the unique reduced row echelon form). The slots
+//       warp's slot, and every other row with bit c set XORs it in (rows
+//       above and below: Gauss-Jordan, so the result is the unique reduced
+//       row echelon form). The slots
 //       alternate with the column's parity, so a slot is rewritten only after
 //       the next column's barrier, when every read of it is done. A row not
 //       yet used as a pivot is zero in every column left of c (each earlier
@@ -40,7 +40,7 @@ namespace hlf {
 
 template <int W, int MAXN>
 struct FactorSmem {
-    int first[2][32];        // per warp: its lowest candidate row for the column (by column parity)
+    int first[2][32];        // per warp: its lowest candidate's key for the column (by column parity)
     uint64_t crow[2][32][W];  // and that row's words
     int pivcol[MAXN];
     uint32_t pivmask[MAXN / 32];
@@ -50,11 +50,12 @@ struct FactorSmem {
 };
 
 // Transpose a 64 x 64 bit block held by one warp: lane l has rows l (x0) and
-// l + 32 (x1), bit s of a row being column s. Each stage j swaps bit j of the
-// row index with bit j of the column index, i.e. exchanges the bits at column
-// s + j of row t with those at column s of row t + j (bit j of s and of t
-// clear); the six stages compose to the transpose. Stage 32 pairs the two rows
-// of a lane, the others pair lanes l and l ^ j.
+// l + 32 (x1), bit s of a row being column s. Stage j (j = 32, 16, ..., 1)
+// swaps the row-index bit of weight j with the column-index bit of weight j:
+// it exchanges the bits at column s + j of row t with those at column s of
+// row t + j, for s and t with that bit clear. The six stages compose to the
+// transpose. Stage 32 pairs the two rows of a lane, the others pair lanes l
+// and l ^ j.
 __device__ __forceinline__ void transpose64_warp(uint64_t& x0, uint64_t& x1, int lane)
 {
     {

@@ -42,7 +42,7 @@
  *   the space) are written to the handle's device status word and returned
  *   by the next call that synchronises on the handle (hlf_get_rank,
  *   hlf_get_factor, hlf_get_status, and the first enumerate call after
- *   hlf_factor).
+ *   hlf_factor other than hlf_enumerate_store_upto, which does not wait).
  */
 #ifndef HLF_H
 #define HLF_H

@@ -12,10 +12,11 @@ Continuous batching (Server.run):
   * admission by device memory: a request is admitted, in arrival order, once
     it has arrived and its output window (want x W words) fits in the device
     staging ring; a window that does not fit waits for earlier ones to leave;
-  * factorisations are launched on high-priority factor streams as requests
-    are admitted
-    and stay resident (one handle each) until their window has reached the
-    host;
+  * factorisations are launched on high-priority factor streams, in turn, as
+    requests are admitted, and stay resident (one handle each) until their
+    window has reached the host. A stream's factor kernels finish in order,
+    so the loop keeps one queue per factor stream and asks only each queue's
+    head whether it is done;
   * every tick, all admitted windows whose factorisation has finished are
     materialised by ONE hlf_enumerate_store_many launch on the enumeration
     stream, into the staging ring, while earlier ticks' windows are still

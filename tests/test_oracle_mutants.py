@@ -28,6 +28,8 @@ MUTANTS = {
     "fold_or_not_xor": ("t->fold[w] ^= z[w];", "t->fold[w] |= z[w];"),
     "paper_counter_bit": ("R[piv[j - 1]] = r - j < 64 ? (uint8_t)((t >> (r - j)) & 1) : 0;",
                           "R[piv[j - 1]] = r - j < 64 ? (uint8_t)((t >> (j - 1 + (j == r))) & 1) : 0;"),
+    "paper_counter_reversed": ("R[piv[j - 1]] = r - j < 64 ? (uint8_t)((t >> (r - j)) & 1) : 0;",
+                               "R[piv[j - 1]] = j - 1 < 64 ? (uint8_t)((t >> (j - 1)) & 1) : 0;"),
     "rref_skips_rows_above": ("if (i == rank || !M[(size_t)i * cols + c]) continue;",
                               "if (i <= rank || !M[(size_t)i * cols + c]) continue;"),
 }
@@ -46,6 +48,7 @@ def _pins_hold() -> bool:
         *(lambda c=c: pins.test_reduce_against_bruteforce_set(*c) for c in pins.TINY[::6]),
         lambda: pins.test_reduce_xor_fold_closed_forms(0),
         *(lambda c=c: pins.test_paper_order_same_set(*c) for c in pins.TINY[:18:3]),
+        *(lambda c=c: pins.test_paper_order_counter_recovered(*c) for c in pins.TINY[:18:3]),
     ]
     for chk in checks:
         try:

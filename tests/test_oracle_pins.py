@@ -288,19 +288,98 @@ def test_large_n_factor_consistency():
     assert not F.z0[F.piv].any()
 
 
+def _leftmost_independent_columns(A: np.ndarray) -> list[int]:
+    """P = L_ind of §2, by its definition: scan the columns left to right and
+    keep each one that is not in the span of those kept (spans held as sets
+    of Python-int bit masks; independent of the oracle's elimination)."""
+    n = A.shape[0]
+    basis: dict[int, int] = {}  # leading bit -> reduced vector
+    keep = []
+    for c in range(n):
+        v = int("".join(str(int(b)) for b in A[::-1, c]), 2)
+        while v:
+            top = v.bit_length() - 1
+            if top not in basis:
+                basis[top] = v
+                keep.append(c)
+                break
+            v ^= basis[top]
+    return keep
+
+
+def _counter_of(R_P: np.ndarray) -> int:
+    """The §4 counter value of R^(r) = R_{p_1} .. R_{p_r} read as a binary
+    numeral with R_{p_1} most significant."""
+    r = len(R_P)
+    return sum(int(R_P[j - 1]) << (r - j) for j in range(1, r + 1))
+
+
+@pytest.mark.parametrize("name,A", [c for c in TINY if 0 < c[1].shape[0] <= 10][:24],
+                         ids=[c[0] for c in TINY if 0 < c[1].shape[0] <= 10][:24])
+def test_paper_order_counter_recovered(name, A):
+    """§2 Eq. 3 with the counter of §4: every solution the paper-order
+    enumeration emits at counter t gives t back. From z alone: z^a is the
+    brute-force solution that vanishes on P, and R_P is the one choice among
+    all 2^r with (A R)|_P = (z ^ z^a)|_P (A[P,P] is nonsingular), found by
+    trying every choice; t is then R^(r) read most significant first."""
+    F = oc.factor(A)
+    P = _leftmost_independent_columns(A)
+    r = len(P)
+    assert r == F.r
+    S = od.solutions_bruteforce(A)
+    za = [z for z in S if not np.any(z[P])]
+    assert len(za) == 1
+    za = za[0].astype(np.int64)
+    # all 2^r choices of R_P and the pivot rows of A R they give
+    choices = od.all_vectors(r).astype(np.int64)  # [2^r][r]
+    App = A[np.ix_(P, P)].astype(np.int64)
+    images = (choices @ App.T) % 2
+    key = {tuple(y): R for y, R in zip(images.tolist(), choices)}
+    assert len(key) == 1 << r  # A[P,P] nonsingular: the choice is unique
+    Z = oc.unpack_rows(oc.paper_order(F, 0, 1 << r), F.n).astype(np.int64)
+    for t, z in enumerate(Z):
+        R_P = key[tuple(((z ^ za)[P]).tolist())]
+        assert _counter_of(R_P) == t, (t, R_P)
+
+
+def _gf2_solve(M: np.ndarray, rhs: np.ndarray) -> np.ndarray:
+    """x with M x = rhs over GF(2) for a square nonsingular 0/1 matrix M,
+    by elimination on Python-int row masks (written here, independent of the
+    oracle's byte-per-bit elimination)."""
+    m = M.shape[0]
+    rows = [(int("".join(str(int(b)) for b in M[i, ::-1]), 2), int(rhs[i])) for i in range(m)]
+    for c in range(m):
+        p = next(i for i in range(c, m) if (rows[i][0] >> c) & 1)
+        rows[c], rows[p] = rows[p], rows[c]
+        for i in range(m):
+            if i != c and (rows[i][0] >> c) & 1:
+                rows[i] = (rows[i][0] ^ rows[c][0], rows[i][1] ^ rows[c][1])
+    return np.array([rows[i][1] for i in range(m)], dtype=np.int64)
+
+
 def test_paper_order_beyond_64_pivots():
-    """r > 64: the paper order's 64-bit counter reaches the first 2^64 values;
-    each is a valid solution and the counter is recovered from z on the
-    pivots (bit r-j of t is R_{p_j}, and z restricted to P determines R)."""
+    """r > 64: the paper order's 64-bit counter reaches the first 2^64 values.
+    Each emitted z is a valid solution, the z are distinct, and the counter is
+    recovered from z: R_P solves A[P,P] R_P = (z ^ z^a)|_P (solved here by a
+    separate GF(2) elimination), the leading r - 64 entries are 0, and the
+    rest read as a binary numeral (R_{p_1} most significant) give t."""
     A = synth.grid_instance(20, 0.5, 1234)
     F = oc.factor(A)
     assert F.r > 64
+    P = _leftmost_independent_columns(A)
+    assert P == [int(p) for p in F.piv[:F.r]]
+    App = A[np.ix_(P, P)]
+    za = F.z0.astype(np.int64)
     top = 1 << 64
     for t0, cnt in ((0, 300), (top - 300, 300), ((1 << 63) - 5, 10)):
         Z = oc.unpack_rows(oc.paper_order(F, t0, cnt), F.n).astype(np.int64)
         par = (Z @ F.X.T.astype(np.int64)) % 2
         assert np.array_equal(par, np.broadcast_to(F.q // 2, par.shape))
         assert len({tuple(z) for z in Z}) == cnt
+        for k in range(0, cnt, 7):
+            R_P = _gf2_solve(App, (Z[k] ^ za)[P])
+            assert not R_P[:F.r - 64].any()
+            assert _counter_of(R_P) == t0 + k
 
 
 def test_dense_stream_layout():

@@ -333,11 +333,14 @@ hlf_status hlf_batch_destroy(hlf_batch* b);
  * item; 2^23 polls per wait). count > HLF_BATCH_NOALLOC_MAX returns
  * HLF_ERR_SIZE and enqueues nothing. A bounded wait that runs out cannot be
  * reported separately here; it shows as red_dev[b].count below
- * min(2^r_b, cap).
+ * min(2^r_b, cap), which a caller checks to detect it.
  *
  * The first call on each device looks up the workspace's device address
- * (with that device current); make that first call before any stream
- * capture. Every call shares the one workspace, and each call clears what must
+ * (with that device current). CUDA loads a library's device code lazily by
+ * default, so that first call may also load the module and reserve the
+ * workspace, which can allocate and synchronise: make one call (a warm-up
+ * with count = 1 is enough) before the region that must not allocate, and
+ * before any stream capture. Later calls allocate nothing. Every call shares the one workspace, and each call clears what must
  * start at zero, so calls whose work overlaps on the GPU (on different streams,
  * or from different host threads) race and give wrong results: issue them in
  * one stream order.

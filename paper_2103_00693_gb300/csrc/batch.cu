@@ -314,7 +314,7 @@ hlf_status hlf_batch_factor_reduce(hlf_batch* b, const uint64_t* A_dev, const in
     a.cap = cap;
     a.chunk = b->chunk;
     const uint64_t cpi = (cap + b->chunk - 1) / b->chunk;
-    if (cpi > (1u << 20) || (uint64_t)count * (cpi + 1) > 0xffffffffull) return HLF_ERR_RANGE;
+    if (cpi > (1u << 20)) return HLF_ERR_RANGE;
     a.chunks_per_inst = (uint32_t)cpi;
     a.r_out = r_dev;
     a.red_out = red_dev;
@@ -327,10 +327,6 @@ hlf_status hlf_batch_factor_reduce(hlf_batch* b, const uint64_t* A_dev, const in
     // With debug flag 1 the queue starts after the factor items, so no ready
     // flag is ever set and every chunk's bounded wait runs out.
     a.first_item = (b->debug & 1u) ? (uint32_t)count : 0u;
-    if (cudaMemsetAsync(b->counter, 0, sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMemsetAsync(b->ready, 0, sizeof(int32_t) * (size_t)count, s) != cudaSuccess ||
-        cudaMemsetAsync(red_dev, 0, sizeof(hlf_reduce) * (size_t)count, s) != cudaSuccess)
-        return HLF_ERR_CUDA;
     const size_t smem = hlf::batch_smem_bytes();
     int fit = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, hlf::batch_kernel, hlf::kThreads, smem) != cudaSuccess ||
@@ -338,6 +334,13 @@ hlf_status hlf_batch_factor_reduce(hlf_batch* b, const uint64_t* A_dev, const in
         return HLF_ERR_CUDA;
     const int per_sm = (b->ctas_per_sm > 0 && b->ctas_per_sm < fit) ? b->ctas_per_sm : fit;
     const int grid = hlf::sm_count() * per_sm;
+    // The 32-bit queue counter is incremented once per item and once more by
+    // every CTA when it finds the queue empty; it must not wrap.
+    if ((uint64_t)count * (cpi + 1) + (uint64_t)grid > 0xffffffffull) return HLF_ERR_RANGE;
+    if (cudaMemsetAsync(b->counter, 0, sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(b->ready, 0, sizeof(int32_t) * (size_t)count, s) != cudaSuccess ||
+        cudaMemsetAsync(red_dev, 0, sizeof(hlf_reduce) * (size_t)count, s) != cudaSuccess)
+        return HLF_ERR_CUDA;
     hlf::batch_kernel<<<grid, hlf::kThreads, smem, s>>>(a);
     if (cudaGetLastError() != cudaSuccess) return HLF_ERR_CUDA;
     // While the stream is being captured into a CUDA graph the event is not

@@ -325,7 +325,10 @@ def hlf_batch_factor_reduce_noalloc(A_dev, word_off_dev, n_dev, count: int, cap:
     """hlf_batch_factor_reduce without a plan and without any allocation in
     the library: for callers that cannot allocate device memory when they
     call (see include/hlf.h). At most BATCH_NOALLOC_MAX matrices per call;
-    calls must not overlap on the GPU."""
+    calls must not overlap on the GPU. The first call on a device may load
+    the library's device code and so allocate: warm up before a region that
+    must not. A bounded wait that ran out shows only as red[b].count below
+    min(2^r[b], cap): compare the two to detect it."""
     _check(load().hlf_batch_factor_reduce_noalloc(_ptr(A_dev), _ptr(word_off_dev), _ptr(n_dev), count, cap,
                                                   _ptr(r_dev), _ptr(red_dev), _stream_ptr(stream)),
            "hlf_batch_factor_reduce_noalloc")

@@ -13,7 +13,13 @@
                log-uniform in 2^10..2^24 solutions, returned to the host.
 
 The ranks quoted above are what the seeded matrices have; they are facts
-about the inputs that the tests recompute, not inputs themselves.
+about the inputs that the tests recompute, not inputs themselves. Both
+headline single instances are full rank (r = n maximises 2^r), where the
+RREF basis is the identity and z^a = 0. The parity tests therefore also run
+each of these two workloads at full size on a seed of lower rank:
+
+* grid3x3 seed 9: r = 6, z^a != 0, pivots {0, 3, 4, 5, 6, 8};
+* grid6x6 seed 1: r = 34, z^a != 0, free columns 33 and 35.
 """
 
 from __future__ import annotations
@@ -22,6 +28,8 @@ from . import grid
 
 GRID3 = dict(N=3, p=0.5, seed=5)
 GRID6 = dict(N=6, p=1.0, seed=3)
+GRID3_LOWRANK = dict(N=3, p=0.5, seed=9)
+GRID6_LOWRANK = dict(N=6, p=1.0, seed=1)
 GRID6_STORE_LOG2 = 30
 GRID8 = dict(N=8, p=0.5, seed=0)
 GRID8_WINDOW_LOG2 = 40
@@ -39,6 +47,14 @@ def grid3():
 
 def grid6():
     return grid.grid_instance(GRID6["N"], GRID6["p"], GRID6["seed"])
+
+
+def grid3_lowrank():
+    return grid.grid_instance(GRID3_LOWRANK["N"], GRID3_LOWRANK["p"], GRID3_LOWRANK["seed"])
+
+
+def grid6_lowrank():
+    return grid.grid_instance(GRID6_LOWRANK["N"], GRID6_LOWRANK["p"], GRID6_LOWRANK["seed"])
 
 
 def grid8():

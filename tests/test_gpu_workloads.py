@@ -1,11 +1,14 @@
 """The single-instance workloads at full size, in the launch configuration
 the benchmark times.
 
-* grid3x3: every solution, against the oracle and the brute-force set.
+* grid3x3: every solution, against the oracle and the brute-force set, on
+  the headline seed (r = n) and on a seed with r = 6 and z^a != 0, where the
+  brute-force comparison is not trivially every string.
 * grid6x6: the full 2^36 reduce against the oracle's full reduce (all host
   cores) and the closed forms (count 2^r, XOR-fold 0); the first 2^30
   solutions stored to HBM, checked on sampled blocks against the oracle and on
-  a 2^20 sample for validity and index recovery.
+  a 2^20 sample for validity and index recovery. The same two tests run on a
+  seed with r = 34 and z^a != 0 (full 2^34 reduce, first 2^30 stored).
 * grid8x8: the 2^40 window reduced whole and in 2^24-solution chunks; chunks
   combine to the whole; 64 seeded chunks against the oracle; 2^20 sampled
   indices checked for validity against Ker(A) and for index recovery on the
@@ -45,11 +48,14 @@ def check_valid_and_indexed(F, Z_words: np.ndarray, idx: np.ndarray):
     assert np.array_equal(gray_inverse(g), idx.astype(np.uint64))
 
 
-def test_grid3x3_all_solutions(cuda_ok):
-    A = wl.grid3()
+@pytest.mark.parametrize("which", ["headline", "lowrank"])
+def test_grid3x3_all_solutions(cuda_ok, which):
+    A = wl.grid3() if which == "headline" else wl.grid3_lowrank()
     F = oc.factor(A)
     G = hlf.Factorization.from_dense(A)
     assert G.rank == F.r
+    if which == "lowrank":
+        assert F.r == 6 and F.z0.any()
     out = G.store(0, 1 << F.r).cpu().numpy().view(np.uint64)
     assert np.array_equal(out, oc.window(F, 0, 1 << F.r))
     S = od.solutions_bruteforce(A)
@@ -57,10 +63,14 @@ def test_grid3x3_all_solutions(cuda_ok):
     G.close()
 
 
-@pytest.fixture(scope="module")
-def grid6(cuda_ok):
-    A = wl.grid6()
+@pytest.fixture(scope="module", params=["headline", "lowrank"])
+def grid6(cuda_ok, request):
+    A = wl.grid6() if request.param == "headline" else wl.grid6_lowrank()
     F = oc.factor(A)
+    if request.param == "lowrank":
+        assert F.r == 34 and F.z0.any()
+    else:
+        assert F.r == 36
     G = hlf.Factorization.from_dense(A)
     yield F, G
     G.close()
@@ -68,9 +78,9 @@ def grid6(cuda_ok):
 
 def test_grid6x6_full_reduce(grid6):
     F, G = grid6
-    assert G.rank == F.r == 36
+    assert G.rank == F.r
     got = hlf.ReduceResult.from_words(G.reduce(0, 1 << F.r).cpu().numpy(), F.W)
-    assert got.count == 1 << 36
+    assert got.count == 1 << F.r
     assert not got.xor_fold.any()  # affine space of dimension >= 2
     c, h, f = oc.reduce(F, 0, 1 << F.r)
     assert (got.count, got.hsum) == (c, h) and np.array_equal(got.xor_fold, f)

@@ -65,6 +65,28 @@ def test_noalloc_matches_planned_on_two_calls(cuda_ok):
     torch.cuda.synchronize()
 
 
+def test_noalloc_call_reserves_no_device_memory(cuda_ok):
+    """After a warm-up call (which may load the device code and reserve the
+    workspace), a call leaves the device's free memory exactly as it was."""
+    import torch
+
+    mats = synth.batch_instances(64, 4, 16, 0.5, 2026)
+    args = _device_batch(mats)
+    count, cap = len(mats), 1 << 12
+    r = torch.empty(count, dtype=torch.int32, device="cuda")
+    red = torch.empty((count, hlf.REDUCE_WORDS), dtype=torch.int64, device="cuda")
+    hlf.hlf_batch_factor_reduce_noalloc(*args, count, cap, r, red)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    hlf.hlf_batch_factor_reduce_noalloc(*args, count, cap, r, red)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    want_r, want_red = _planned(*args, count, cap)
+    assert np.array_equal(r.cpu().numpy(), want_r)
+    assert np.array_equal(red.cpu().numpy(), want_red)
+
+
 def test_noalloc_rejects_more_than_the_maximum(cuda_ok):
     import torch
 

@@ -89,6 +89,14 @@ const char* hlf_status_string(hlf_status s);
 /* Number of CUDA devices visible, or -1 if the runtime cannot be reached. */
 int32_t hlf_device_count(void);
 
+/* Host-side fault injection for tests of a caller's failure paths (the
+ * paper has no counterpart): the next `count` calls that allocate
+ * (hlf_factor, hlf_many_create, hlf_batch_create) return HLF_ERR_NOMEM after
+ * their argument checks, as if their host or device allocation had failed,
+ * without touching the GPU. count = 0 clears it; count < 0 is HLF_ERR_ARG.
+ * Process-wide, shared by all threads. */
+hlf_status hlf_debug_fail_allocs(int32_t count);
+
 /*
  * Stage 1, the CLA module (Section 2, steps (1)-(4); Fig. 1(b)).
  * A_dev:  [n][W] uint64, device, caller-owned; read until the factor kernel

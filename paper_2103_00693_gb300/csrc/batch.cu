@@ -231,6 +231,7 @@ hlf_status hlf_batch_create(int32_t max_instances, hlf_batch** out)
     if (!out) return HLF_ERR_ARG;
     *out = nullptr;
     if (max_instances < 1 || max_instances > (1 << 24)) return HLF_ERR_ARG;
+    if (hlf::take_injected_alloc_failure()) return HLF_ERR_NOMEM;
     hlf_batch* b = new (std::nothrow) hlf_batch;
     if (!b) return HLF_ERR_NOMEM;
     b->max_instances = max_instances;

@@ -1,6 +1,7 @@
 // C ABI of libhlf (declared in include/hlf.h): argument checks, the handle
 // and its device buffers, and the launches of the stage-1 and stage-2 kernels.
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -257,6 +258,18 @@ void keep_pool_memory()
     done[dev] = true;
 }
 
+namespace {
+std::atomic<int32_t> g_fail_allocs{0};
+}
+
+bool take_injected_alloc_failure()
+{
+    int32_t v = g_fail_allocs.load(std::memory_order_relaxed);
+    while (v > 0)
+        if (g_fail_allocs.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return true;
+    return false;
+}
+
 int sm_count()
 {
     static int cache[64] = {0};
@@ -290,6 +303,13 @@ const char* hlf_status_string(hlf_status s)
     return "unknown status";
 }
 
+hlf_status hlf_debug_fail_allocs(int32_t count)
+{
+    if (count < 0) return HLF_ERR_ARG;
+    hlf::g_fail_allocs.store(count, std::memory_order_relaxed);
+    return HLF_OK;
+}
+
 int32_t hlf_device_count(void)
 {
     int n = 0;
@@ -303,6 +323,7 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
     *out = nullptr;
     if (!A_dev) return HLF_ERR_ARG;
     if (n < 1 || n > HLF_MAX_N) return HLF_ERR_SIZE;
+    if (hlf::take_injected_alloc_failure()) return HLF_ERR_NOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     hlf_handle* h = new (std::nothrow) hlf_handle;
     if (!h) return HLF_ERR_NOMEM;

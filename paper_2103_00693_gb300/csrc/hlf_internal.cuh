@@ -57,6 +57,11 @@ int sm_count();
 // handle memory (called before the first stream-ordered allocation).
 void keep_pool_memory();
 
+// Host-side fault injection (hlf_debug_fail_allocs): true if the calling
+// entry point must fail its allocation with HLF_ERR_NOMEM; consumes one
+// pending failure.
+bool take_injected_alloc_failure();
+
 // ----------------------------------------------------------- device helpers
 
 // SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014): the

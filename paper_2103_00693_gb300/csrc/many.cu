@@ -181,6 +181,7 @@ hlf_status hlf_many_create(int32_t max_windows, hlf_many** out)
     if (!out) return HLF_ERR_ARG;
     *out = nullptr;
     if (max_windows < 1 || max_windows > (1 << 22)) return HLF_ERR_ARG;
+    if (hlf::take_injected_alloc_failure()) return HLF_ERR_NOMEM;
     hlf_many* m = new (std::nothrow) hlf_many;
     if (!m) return HLF_ERR_NOMEM;
     m->max_windows = max_windows;

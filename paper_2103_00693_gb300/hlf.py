@@ -40,6 +40,7 @@ _i32 = ctypes.c_int32
 SIGNATURES = {
     "hlf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hlf_device_count": (_i32, []),
+    "hlf_debug_fail_allocs": (ctypes.c_int, [_i32]),
     "hlf_factor": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_vp)]),
     "hlf_get_rank": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "hlf_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -167,6 +168,12 @@ def hlf_status_string(status: int) -> str:
 
 def hlf_device_count() -> int:
     return int(load().hlf_device_count())
+
+
+def hlf_debug_fail_allocs(count: int):
+    """Fault injection for tests: the next `count` allocating calls fail with
+    HLF_ERR_NOMEM (host-side; no GPU involved)."""
+    _check(load().hlf_debug_fail_allocs(count), "hlf_debug_fail_allocs")
 
 
 def hlf_factor(A_dev, n: int, stream=None) -> int:

@@ -9,15 +9,18 @@ Once its factorisation is known (rank r), the window is
 and the solutions z(offset) .. z(offset + count - 1) are returned to the host.
 
 Continuous batching (Server.run):
-  * admission by device memory: a request is admitted, in arrival order, once
-    it has arrived and its output window (want x W words) fits in the device
-    staging ring; a window that does not fit waits for earlier ones to leave;
-  * factorisations are launched on high-priority factor streams, in turn, as
-    requests are admitted, and stay resident (one handle each) until their
-    window has reached the host. A stream's factor kernels finish in order,
-    so the loop keeps one queue per factor stream and asks only each queue's
-    head whether it is done;
-  * every tick, all admitted windows whose factorisation has finished are
+  * admission in arrival order: a request that has arrived is checked on the
+    host (a square 0/1 matrix, n in [1, 1024], want >= 1), its packed matrix
+    is carved from a device ring, and its factorisation is launched on one of
+    several high-priority factor streams, in turn. A stream's factor kernels
+    finish in order, so the loop keeps one queue per factor stream and asks
+    only each queue's head whether it is done;
+  * admission by device memory: once the rank r is known, the request's
+    output window (min(want, 2^min(r,64)) x W words, no more) is reserved in
+    the device staging ring and the pinned host ring, in factorisation order;
+    a window that does not fit yet waits for earlier ones to leave, and the
+    factorisation stays resident (one handle) meanwhile;
+  * every tick, all factored windows that got their memory are
     materialised by ONE hlf_enumerate_store_many launch on the enumeration
     stream, into the staging ring, while earlier ticks' windows are still
     being copied out and later requests are being factored;
@@ -28,6 +31,22 @@ Both rings are allocated once, up front, so the loop itself never allocates
 or frees memory (allocation can synchronise the device); handles use the
 stream-ordered pool. All solver work runs in the library's kernels; this
 module only schedules.
+
+Failure paths. Every request ends in exactly one outcome, and one request's
+failure never disturbs another's result:
+  * "ok": the window reached the host (q.result);
+  * "failed": q.status is the hlf_status that ended it -- a host-side check
+    (HLF_ERR_ARG, HLF_ERR_SIZE), a fault the factor kernel found
+    (HLF_ERR_NOT_SYMMETRIC, HLF_ERR_PADDING: the problem of Section 1 is
+    defined for symmetric A only), or an allocation the library could not
+    make (HLF_ERR_NOMEM);
+  * "refused": the request can never fit the rings (its packed matrix or its
+    window is larger than the ring), status HLF_ERR_NOMEM;
+  * "cancelled": Server.cancel(id), or the request's own t_cancel time,
+    reached it before its window was launched (waiting, being factored, or
+    factored and waiting for memory). A request already launched completes
+    normally.
+Whatever a request held (ring blocks, its handle) is released when it ends.
 """
 
 from __future__ import annotations
@@ -111,13 +130,21 @@ class Ring:
             self.head = self.tail = 0
 
 
+OK, FAILED, CANCELLED, REFUSED = "ok", "failed", "cancelled", "refused"
+_ERR_ARG = 1
+_ERR_SIZE = 2
+_ERR_NOMEM = 6
+
+
 @dataclass
 class Req:
     id: int
     t_arrival: float
-    A: np.ndarray
+    A: np.ndarray | None
     want: int
     u: int
+    A_words: np.ndarray | None = None  # packed rows [n][W], given instead of A
+    t_cancel: float | None = None
     n: int = 0
     W: int = 0
     r: int = -1
@@ -125,6 +152,10 @@ class Req:
     count: int = 0
     t_done: float = 0.0
     result: np.ndarray | None = None
+    outcome: str = ""
+    status: int = 0
+    state: str = "waiting"  # waiting, factoring, pending, launched, done
+    cancel_requested: bool = False
     h: int = 0
     blk_dev: list | None = None
     blk_host: list | None = None
@@ -146,6 +177,9 @@ class Stats:
     busy_s: float = 0.0
     ticks: int = 0
     launches: int = 0
+    failed: int = 0
+    cancelled: int = 0
+    refused: int = 0
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
@@ -155,7 +189,8 @@ class Stats:
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "makespan_s": self.makespan_s,
                 "busy_frac": self.busy_s / self.makespan_s if self.makespan_s else 0.0,
-                "ticks": self.ticks, "launches": self.launches}
+                "ticks": self.ticks, "launches": self.launches,
+                "failed": self.failed, "cancelled": self.cancelled, "refused": self.refused}
 
 
 @contextlib.contextmanager
@@ -174,7 +209,39 @@ def _no_gc_pauses():
 
 
 def _mk_reqs(stream: list[dict]) -> list[Req]:
-    return [Req(id=q["id"], t_arrival=q["t_arrival"], A=q["A"], want=q["want"], u=q["u"]) for q in stream]
+    return [Req(id=q["id"], t_arrival=q["t_arrival"], A=q.get("A"), want=q["want"], u=q["u"],
+                A_words=q.get("A_words"), n=int(q.get("n", 0)), t_cancel=q.get("t_cancel"))
+            for q in stream]
+
+
+def check_request(q: Req) -> tuple[int, np.ndarray | None]:
+    """Host-side checks of a request before anything is launched: (status,
+    packed rows). A dense A must be a square 0/1 matrix; packed rows must be
+    [n][W] words; n must lie in [1, 1024]; want must be >= 1. Symmetry and
+    padding bits are left to the factor kernel, which reports them in the
+    request's own status word."""
+    if q.want < 1:
+        return _ERR_ARG, None
+    if q.A_words is not None:
+        w = np.asarray(q.A_words)
+        if w.ndim != 2 or w.dtype.itemsize != 8:
+            return _ERR_ARG, None
+        if not 1 <= q.n <= hlf.MAX_N:
+            return _ERR_SIZE, None
+        if w.shape != (q.n, hlf.words(q.n)):
+            return _ERR_ARG, None
+        return 0, np.ascontiguousarray(w).view(np.int64)
+    if q.A is None:
+        return _ERR_ARG, None
+    A = np.asarray(q.A)
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        return _ERR_ARG, None
+    q.n = A.shape[0]
+    if not 1 <= q.n <= hlf.MAX_N:
+        return _ERR_SIZE, None
+    if A.size and (A.min() < 0 or A.max() > 1):
+        return _ERR_ARG, None
+    return 0, hlf.pack_rows(A).view(np.int64)
 
 
 class Server:
@@ -185,7 +252,7 @@ class Server:
     """
 
     def __init__(self, device_bytes: int = 8 << 30, host_bytes: int = 8 << 30, max_batch: int = 4096,
-                 keep_results: bool = True):
+                 keep_results: bool = True, matrix_bytes: int = 64 << 20):
         import torch
 
         self.keep = keep_results
@@ -199,10 +266,11 @@ class Server:
         self.many = hlf.hlf_many_create(max_batch)
         self.dev_ring = Ring(torch.empty(device_bytes // 8, dtype=torch.int64, device="cuda"))
         self.host_ring = Ring(torch.empty(host_bytes // 8, dtype=torch.int64, pin_memory=True))
-        self.in_ring = Ring(torch.empty((64 << 20) // 8, dtype=torch.int64, pin_memory=True))
+        self.in_ring = Ring(torch.empty(matrix_bytes // 8, dtype=torch.int64, pin_memory=True))
         # the packed matrices on the device: carved from a ring as well, so
         # the loop never reaches the allocator (which may synchronise)
-        self.mat_ring = Ring(torch.empty((64 << 20) // 8, dtype=torch.int64, device="cuda"))
+        self.mat_ring = Ring(torch.empty(matrix_bytes // 8, dtype=torch.int64, device="cuda"))
+        self._cancel: set = set()
 
     def close(self):
         if self.many:
@@ -215,81 +283,214 @@ class Server:
         except Exception:
             pass
 
-    def _admit(self, q: Req) -> bool:
+    def cancel(self, req_id: int):
+        """Ask the running loop to cancel a request. It takes effect at the
+        loop's next iteration if the request's window has not been launched
+        yet; otherwise the request completes normally."""
+        self._cancel.add(req_id)
+
+    # ------------------------------------------------------------ internals
+
+    def _release(self, q: Req):
+        """Give back whatever q holds: its handle and its ring blocks."""
+        if q.h:
+            hlf.hlf_destroy(q.h)
+            q.h = 0
+        q.A_dev = None
+        for ring, name in ((self.in_ring, "blk_in"), (self.mat_ring, "blk_mat"),
+                           (self.dev_ring, "blk_dev"), (self.host_ring, "blk_host")):
+            blk = getattr(q, name)
+            if blk is not None:
+                ring.free(blk)
+                setattr(q, name, None)
+
+    def _finish(self, q: Req, outcome: str, status: int, st: Stats, done: list, t: float):
+        q.outcome, q.status, q.state, q.t_done = outcome, status, "done", t
+        if outcome == OK:
+            st.latencies_ms.append(1e3 * (q.t_done - q.t_arrival))
+            st.solutions += q.count
+            st.bytes_out += q.count * q.W * 8
+        elif outcome == FAILED:
+            st.failed += 1
+        elif outcome == CANCELLED:
+            st.cancelled += 1
+        else:
+            st.refused += 1
+        done.append(q)
+        if self._on_event:
+            self._on_event("done", q)
+
+    def _admit(self, q: Req, st: Stats, done: list, t: float) -> bool:
+        """Try to admit the head of the waiting queue. Returns False if it
+        must wait for ring space; True if it left the queue (admitted, or
+        ended by a host-side check or a failed launch)."""
         import torch
 
-        q.n = q.A.shape[0]
+        status, packed = check_request(q)
+        if status:
+            self._finish(q, FAILED, status, st, done, t)
+            return True
         q.W = hlf.words(q.n)
-        words = q.want * q.W
-        bd = self.dev_ring.alloc(words)
-        if bd is None:
-            return False
-        bh = self.host_ring.alloc(words)
-        if bh is None:
-            self.dev_ring.free(bd)
-            return False
-        bi = self.in_ring.alloc(q.n * q.W)
-        bm = self.mat_ring.alloc(q.n * q.W) if bi is not None else None
+        nw = q.n * q.W
+        if nw > self.in_ring.size or nw > self.mat_ring.size:
+            self._finish(q, REFUSED, _ERR_NOMEM, st, done, t)
+            return True
+        bi = self.in_ring.alloc(nw)
+        bm = self.mat_ring.alloc(nw) if bi is not None else None
         if bm is None:
             if bi is not None:
                 self.in_ring.free(bi)
-            self.dev_ring.free(bd)
-            self.host_ring.free(bh)
             return False
-        q.blk_dev, q.blk_host, q.blk_in, q.blk_mat = bd, bh, bi, bm
-        staged = self.in_ring.view(bi, q.n * q.W)
-        staged.copy_(torch.from_numpy(hlf.pack_rows(q.A).view(np.int64).ravel()))
+        q.blk_in, q.blk_mat = bi, bm
+        staged = self.in_ring.view(bi, nw)
+        staged.copy_(torch.from_numpy(packed.ravel()))
         q.lane = self._next_factor
         sf = self.s_factors[q.lane]
         self._next_factor = (self._next_factor + 1) % len(self.s_factors)
         with torch.cuda.stream(sf):
-            q.A_dev = self.mat_ring.view(bm, q.n * q.W).view(q.n, q.W)
+            q.A_dev = self.mat_ring.view(bm, nw).view(q.n, q.W)
             q.A_dev.view(-1).copy_(staged, non_blocking=True)
-            q.h = hlf.hlf_factor(q.A_dev, q.n, sf)
+            try:
+                q.h = hlf.hlf_factor(q.A_dev, q.n, sf)
+            except hlf.HlfError as e:
+                # the copy above may still be reading the staged rows
+                sf.synchronize()
+                self._release(q)
+                self._finish(q, FAILED, e.status, st, done, t)
+                return True
             q.ev_factor = torch.cuda.Event()
             q.ev_factor.record(sf)
+        q.state = "factoring"
+        if self._on_event:
+            self._on_event("admitted", q)
         return True
 
-    def run(self, stream: list[dict]) -> tuple[Stats, list[Req]]:
+    def _apply_cancels(self, by_id, waiting, pending, st, done, t):
+        """End the requests asked to be cancelled that have not been
+        launched: a waiting or factored one at once, one being factored once
+        its factor kernel is done (its handle and matrix are in use)."""
+        if not self._cancel:
+            return
+        ids, self._cancel = self._cancel, set()
+        for i in ids:
+            q = by_id.get(i)
+            if q is None or q.state in ("launched", "done"):
+                continue
+            if q.state == "waiting":
+                waiting.remove(q)
+                self._finish(q, CANCELLED, 0, st, done, t)
+            elif q.state == "factoring":
+                q.cancel_requested = True
+            elif q.state == "pending":
+                pending.remove(q)
+                self._release(q)
+                self._finish(q, CANCELLED, 0, st, done, t)
+
+    def run(self, stream: list[dict], on_event=None) -> tuple[Stats, list[Req]]:
+        """Serve `stream` (dicts with id, t_arrival, A or A_words + n, want, u,
+        and optionally t_cancel). on_event(kind, req), if given, is called
+        with kind "admitted", "factored", "launched" and "done". Returns the
+        statistics and every request, in completion order."""
+        self._on_event = on_event
         with _no_gc_pauses():
-            return self._run(stream)
+            try:
+                return self._run(stream)
+            finally:
+                self._on_event = None
 
     def _run(self, stream: list[dict]) -> tuple[Stats, list[Req]]:
         import torch
 
         reqs = _mk_reqs(stream)
+        by_id = {q.id: q for q in reqs}
         waiting = collections.deque(reqs)
+        cancels = sorted((q.t_cancel, q.id) for q in reqs if q.t_cancel is not None)
+        next_cancel = 0
         # one FIFO per factor stream: a stream's factor kernels finish in
         # order, so only each queue's head needs an event query
         factoring = [collections.deque() for _ in self.s_factors]
+        pending: collections.deque = collections.deque()  # factored, waiting for window memory
         copying: list[Req] = []
         done: list[Req] = []
         st = Stats(n_requests=len(reqs))
         t0 = time.perf_counter()
         busy_since = None
-        while waiting or any(factoring) or copying:
+        while waiting or any(factoring) or pending or copying:
             now = time.perf_counter() - t0
+            # ---- cancellations (timed ones, then those asked through cancel())
+            while next_cancel < len(cancels) and cancels[next_cancel][0] <= now:
+                self._cancel.add(cancels[next_cancel][1])
+                next_cancel += 1
+            self._apply_cancels(by_id, waiting, pending, st, done, now)
+            # ---- admission: host checks, matrix memory, factor launch
             while waiting and waiting[0].t_arrival <= now:
-                if not self._admit(waiting[0]):
-                    if not (any(factoring) or copying):
-                        raise RuntimeError(f"request {waiting[0].id} does not fit the rings")
+                if not self._admit(waiting[0], st, done, now):
                     break
                 q = waiting.popleft()
-                factoring[q.lane].append(q)
-                if busy_since is None:
-                    busy_since = now
-            ready = []
+                if q.state == "factoring":
+                    factoring[q.lane].append(q)
+                    if busy_since is None:
+                        busy_since = now
+            # ---- finished factorisations: rank, or the kernel's fault
+            progressed = False
             for fq in factoring:
-                while fq and len(ready) < self.max_batch and fq[0].ev_factor.query():
-                    ready.append(fq.popleft())
-            if ready:
-                for q in ready:
+                while fq and fq[0].ev_factor.query():
+                    q = fq.popleft()
+                    progressed = True
+                    # the factor kernel has read the matrix: its blocks are free
                     self.in_ring.free(q.blk_in)
-                    q.r = hlf.hlf_get_rank(q.h)
+                    self.mat_ring.free(q.blk_mat)
+                    q.blk_in = q.blk_mat = None
+                    q.A_dev = None
+                    t = time.perf_counter() - t0
+                    if q.cancel_requested:
+                        self._release(q)
+                        self._finish(q, CANCELLED, 0, st, done, t)
+                        continue
+                    try:
+                        q.r = hlf.hlf_get_rank(q.h)
+                    except hlf.HlfError as e:
+                        self._release(q)
+                        self._finish(q, FAILED, e.status, st, done, t)
+                        continue
                     q.offset, q.count = window_of(q.r, q.want, q.u)
-                hlf.hlf_enumerate_store_many(
-                    self.many, [q.h for q in ready], [q.offset for q in ready], [q.count for q in ready],
-                    [self.dev_ring.view(q.blk_dev, max(q.count, 1) * q.W) for q in ready], self.s_enum)
+                    q.state = "pending"
+                    pending.append(q)
+                    if self._on_event:
+                        self._on_event("factored", q)
+            # ---- window memory, reserved for the window's actual size
+            if self._cancel:
+                self._apply_cancels(by_id, waiting, pending, st, done, time.perf_counter() - t0)
+            ready = []
+            while pending and len(ready) < self.max_batch:
+                q = pending[0]
+                words = q.count * q.W
+                if words > self.dev_ring.size or words > self.host_ring.size:
+                    pending.popleft()
+                    self._release(q)
+                    self._finish(q, REFUSED, _ERR_NOMEM, st, done, time.perf_counter() - t0)
+                    continue
+                bd = self.dev_ring.alloc(words)
+                if bd is None:
+                    break
+                bh = self.host_ring.alloc(words)
+                if bh is None:
+                    self.dev_ring.free(bd)
+                    break
+                q.blk_dev, q.blk_host = bd, bh
+                ready.append(pending.popleft())
+            if ready:
+                try:
+                    hlf.hlf_enumerate_store_many(
+                        self.many, [q.h for q in ready], [q.offset for q in ready], [q.count for q in ready],
+                        [self.dev_ring.view(q.blk_dev, q.count * q.W) for q in ready], self.s_enum)
+                except hlf.HlfError as e:
+                    t = time.perf_counter() - t0
+                    for q in ready:
+                        self._release(q)
+                        self._finish(q, FAILED, e.status, st, done, t)
+                    ready = []
+            if ready:
                 st.ticks += 1
                 st.launches += 1
                 ev = torch.cuda.Event()
@@ -302,30 +503,24 @@ class Server:
                                                                      non_blocking=True)
                         q.ev_copy = torch.cuda.Event()
                         q.ev_copy.record(self.s_copy)
+                        q.state = "launched"
+                        if self._on_event:
+                            self._on_event("launched", q)
                 copying.extend(ready)
             finished = 0
             while copying and copying[0].ev_copy.query():  # copies complete in stream order
                 q = copying.pop(0)
                 finished += 1
-                q.t_done = time.perf_counter() - t0
-                st.latencies_ms.append(1e3 * (q.t_done - q.t_arrival))
-                st.solutions += q.count
-                st.bytes_out += q.count * q.W * 8
                 if self.keep:
                     q.result = self.host_ring.view(q.blk_host, q.count * q.W).numpy().view(np.uint64)\
                         .reshape(q.count, q.W).copy()
-                hlf.hlf_destroy(q.h)
-                q.h = 0
-                q.A_dev = None
-                self.mat_ring.free(q.blk_mat)  # the factor kernel read it long before the copy ended
-                self.dev_ring.free(q.blk_dev)
-                self.host_ring.free(q.blk_host)
-                done.append(q)
-            if busy_since is not None and not (any(factoring) or copying):
+                self._release(q)
+                self._finish(q, OK, 0, st, done, time.perf_counter() - t0)
+            if busy_since is not None and not (any(factoring) or pending or copying):
                 st.busy_s += (time.perf_counter() - t0) - busy_since
                 busy_since = None
-            if not ready and not finished:
-                if waiting and not any(factoring) and not copying:
+            if not ready and not finished and not progressed:
+                if waiting and not any(factoring) and not pending and not copying:
                     dt = waiting[0].t_arrival - (time.perf_counter() - t0)
                     if dt > 0:
                         time.sleep(min(dt, 0.001))
@@ -342,9 +537,10 @@ def run_plain(stream: list[dict], keep_results: bool = True, host_bytes: int = 2
               device_bytes: int = 2 << 30) -> tuple[Stats, list[Req]]:
     """The plain path: requests served one at a time in arrival order, each
     with its own factor launch, window launch and copy to pinned host memory,
-    waiting for each step. It uses the same kind of preallocated buffers and
-    the same collector setting, so it differs from Server.run only in
-    scheduling."""
+    waiting for each step. It uses the same kind of preallocated buffers, the
+    same collector setting and the same outcomes (a request whose t_cancel
+    has passed when its turn comes is cancelled), so it differs from
+    Server.run only in scheduling."""
     with _no_gc_pauses():
         return _run_plain(stream, keep_results, host_bytes, device_bytes)
 
@@ -357,24 +553,55 @@ def _run_plain(stream, keep_results, host_bytes, device_bytes):
     dev_buf = torch.empty(device_bytes // 8, dtype=torch.int64, device="cuda")
     host_buf = torch.empty(host_bytes // 8, dtype=torch.int64, pin_memory=True)
     in_buf = torch.empty((1 << 20) // 8, dtype=torch.int64, pin_memory=True)
+
+    def end(q, outcome, status):
+        q.outcome, q.status, q.state, q.t_done = outcome, status, "done", time.perf_counter() - t0
+        if outcome == FAILED:
+            st.failed += 1
+        elif outcome == CANCELLED:
+            st.cancelled += 1
+        elif outcome == REFUSED:
+            st.refused += 1
+
     t0 = time.perf_counter()
     for q in reqs:
         now = time.perf_counter() - t0
         if q.t_arrival > now:
             time.sleep(q.t_arrival - now)
         t_start = time.perf_counter() - t0
-        q.n = q.A.shape[0]
+        if q.t_cancel is not None and q.t_cancel <= t_start:
+            end(q, CANCELLED, 0)
+            continue
+        status, packed = check_request(q)
+        if status:
+            end(q, FAILED, status)
+            continue
         q.W = hlf.words(q.n)
-        in_buf[: q.n * q.W].copy_(torch.from_numpy(hlf.pack_rows(q.A).view(np.int64).ravel()))
+        if q.n * q.W > in_buf.numel():
+            end(q, REFUSED, _ERR_NOMEM)
+            continue
+        in_buf[: q.n * q.W].copy_(torch.from_numpy(packed.ravel()))
         A_dev = in_buf[: q.n * q.W].view(q.n, q.W).to("cuda", non_blocking=True)
-        h = hlf.hlf_factor(A_dev, q.n)
-        q.r = hlf.hlf_get_rank(h)
+        h = 0
+        try:
+            h = hlf.hlf_factor(A_dev, q.n)
+            q.r = hlf.hlf_get_rank(h)
+        except hlf.HlfError as e:
+            if h:
+                hlf.hlf_destroy(h)
+            torch.cuda.current_stream().synchronize()
+            end(q, FAILED, e.status)
+            continue
         q.offset, q.count = window_of(q.r, q.want, q.u)
         words = q.count * q.W
+        if words > dev_buf.numel() or words > host_buf.numel():
+            hlf.hlf_destroy(h)
+            end(q, REFUSED, _ERR_NOMEM)
+            continue
         hlf.hlf_enumerate_store(h, q.offset, q.count, dev_buf[: max(words, 1)])
         host_buf[:words].copy_(dev_buf[:words])
         hlf.hlf_destroy(h)
-        q.t_done = time.perf_counter() - t0
+        end(q, OK, 0)
         st.busy_s += q.t_done - t_start
         st.launches += 2
         st.latencies_ms.append(1e3 * (q.t_done - q.t_arrival))

@@ -95,3 +95,29 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hbuild, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         mod.load()
+
+
+def test_injected_allocation_failures_are_nomem(lib):
+    """hlf_debug_fail_allocs makes the next allocating calls return
+    HLF_ERR_NOMEM after their argument checks, with no GPU involved; argument
+    errors still come first and do not consume an injected failure."""
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.hlf_debug_fail_allocs(-1) == 1
+    assert lib.hlf_debug_fail_allocs(3) == 0
+    assert lib.hlf_factor(fake, 0, None, ctypes.byref(h)) == 2      # size check first
+    assert lib.hlf_factor(fake, 9, None, ctypes.byref(h)) == 6      # injected
+    assert h.value is None
+    m = ctypes.c_void_p()
+    assert lib.hlf_many_create(16, ctypes.byref(m)) == 6
+    b = ctypes.c_void_p()
+    assert lib.hlf_batch_create(16, ctypes.byref(b)) == 6
+    assert m.value is None and b.value is None
+    assert lib.hlf_debug_fail_allocs(0) == 0
+
+
+def test_package_reexports_every_entry_point():
+    """Every C entry point has a same-named function in the package (the
+    status-string and device-count helpers included)."""
+    missing = [name for name in hlf.SIGNATURES if not hasattr(hlf, name)]
+    assert not missing, missing

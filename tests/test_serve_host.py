@@ -82,3 +82,31 @@ def test_ring_fifo_reuse_and_refusal():
     assert ring.alloc(100) is None
     ring.free(a)
     assert ring.alloc(1024)[0] == 0
+
+
+def test_check_request_statuses():
+    """Host-side request checks: each malformed form maps to its status
+    before anything reaches the GPU; symmetry and padding are left to the
+    factor kernel."""
+    ok = np.eye(5, dtype=np.uint8)
+
+    def req(**kw):
+        base = dict(id=0, t_arrival=0.0, A=ok, want=4, u=0)
+        base.update(kw)
+        return serve._mk_reqs([base])[0]
+
+    assert serve.check_request(req())[0] == 0
+    assert serve.check_request(req(want=0))[0] == 1
+    assert serve.check_request(req(A=np.ones((3, 4), dtype=np.uint8)))[0] == 1
+    assert serve.check_request(req(A=2 * ok))[0] == 1
+    assert serve.check_request(req(A=np.zeros((0, 0), dtype=np.uint8)))[0] == 2
+    assert serve.check_request(req(A=np.zeros((1100, 1100), dtype=np.uint8)))[0] == 2
+    asym = ok.copy()
+    asym[0, 3] = 1
+    assert serve.check_request(req(A=asym))[0] == 0  # the kernel reports it
+    words = np.zeros((70, 2), dtype=np.uint64)
+    assert serve.check_request(req(A=None, A_words=words, n=70))[0] == 0
+    assert serve.check_request(req(A=None, A_words=words, n=71))[0] == 1
+    assert serve.check_request(req(A=None, A_words=words[:, :1], n=70))[0] == 1
+    assert serve.check_request(req(A=None, A_words=np.zeros((2000, 32), np.uint64), n=2000))[0] == 2
+    assert serve.check_request(req(A=None))[0] == 1

@@ -99,6 +99,18 @@ def parse():
     return p.parse_args()
 
 
+def int_peak(dev=None):
+    """(peak 32-bit integer ops/s in T, its basis): every SM's four
+    schedulers issuing one 32-lane instruction per clock at the maximum SM
+    clock."""
+    import torch
+
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device() if dev is None else dev).multi_processor_count
+    peak = sms * ISSUE_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 / 1e12
+    return peak, f"{sms} SMs x {ISSUE_LANES_PER_SM_CLK} int32 lanes/clk x {pk['sm_max_mhz']:.0f} MHz (issue limit)"
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -620,15 +632,25 @@ def run_configs(dev):
     return out
 
 
+def batched_ops(Ws, counts) -> int:
+    """Algorithmic 32-bit integer operations of the batched reduce: the
+    single-instance reduce's 24W - 4 per solution (20 at W = 1), summed over
+    the instances' solution counts; factorisation work is not counted."""
+    return int(sum(int(c) * (24 * int(w) - 4) for w, c in zip(Ws, counts)))
+
+
 def run_batched(args):
     """The batched workload: 4096 grids (N in 4..16, p = 1/2), each reducing
     min(2^r, 2^20) solutions. One persistent launch per step, replayed from a
-    CUDA graph with autotuned tiles, against the plain path (factor + reduce
-    launches per grid)."""
+    CUDA graph with autotuned tiles (warps per item, CTAs per SM, chunk),
+    against the same two stages as separate batched calls
+    (hlf_factor_batched + hlf_enumerate_batched) and against the plain path
+    (a factor launch and a reduce launch per grid, matrices staged on the
+    device beforehand, no host wait in between)."""
     import torch
 
     from paper_2103_00693_gb300 import autotune
-    from paper_2103_00693_gb300.batch import Batch, per_instance
+    from paper_2103_00693_gb300.batch import Batch, PlainPath
     from synth import workloads as wl
 
     mats = wl.batch()
@@ -648,20 +670,44 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     r, red = B.results()
-    sols = sum(x.count for x in red)
+    counts = [x.count for x in red]
+    sols = sum(counts)
+    ops = batched_ops(B.Ws, counts)
+    ipk, ipk_basis = int_peak()
+    # the two-call form of the same work
+    for _ in range(2):
+        B.factor()
+        B.reduce(cap)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        B.factor()
+        B.reduce(cap)
+    e1.record()
+    torch.cuda.synchronize()
+    split_ms = e0.elapsed_time(e1) / reps
     B.close()
-    per_instance(mats[:64], cap)  # warm the plain path
+    plain = PlainPath(mats)
+    plain.run(cap)  # warm-up: pool, module load
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ranks, _ = per_instance(mats, cap)
+    e0.record()
+    plain.run(cap)
+    e1.record()
     torch.cuda.synchronize()
-    plain_s = time.perf_counter() - t0
+    plain_ms = e0.elapsed_time(e1)
     return {"workload": "4096 grids, N uniform 4..16, p=1/2, min(2^r, 2^20) solutions each",
             "ms_per_batch": ms, "inst_per_s": len(mats) / (ms / 1e3), "solutions_per_s": sols / (ms / 1e3),
-            "solutions_per_batch": sols, "tiles": {"ctas_per_sm": tune["tiles"][0], "chunk": tune["tiles"][1]},
+            "solutions_per_batch": sols,
+            "tiles": {"warps_per_item": tune["tiles"][0], "ctas_per_sm": tune["tiles"][1], "chunk": tune["tiles"][2]},
             "launch": "one persistent kernel (+3 memsets) replayed from a CUDA graph",
-            "plain_ms_per_batch": 1e3 * plain_s, "plain_inst_per_s": len(mats) / plain_s,
-            "speedup_vs_plain": plain_s / (ms / 1e3)}
+            "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12, "peak": ipk,
+                         "unit": "Tops/s", "frac": ops / (ms / 1e3) / 1e12 / ipk,
+                         "ops_per_batch": ops, "ops_per_solution": "24W - 4 (20 at W = 1)",
+                         "kernel": "batch_kernel", "peak_basis": ipk_basis},
+            "split_calls_ms_per_batch": split_ms,
+            "plain_ms_per_batch": plain_ms, "plain_inst_per_s": len(mats) / (plain_ms / 1e3),
+            "plain": "per grid: hlf_factor + hlf_enumerate_reduce_upto on one stream, no host wait",
+            "speedup_vs_plain": plain_ms / ms}
 
 
 def run_served(args, srv=None):

@@ -175,6 +175,17 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
 hlf_status hlf_enumerate_store_upto(hlf_handle* h, uint64_t cap, uint64_t* out_dev, void* stream);
 
 /*
+ * Stage 2 reduced for small instances, with no host round trip after
+ * hlf_factor: *red_dev (device, one hlf_reduce, overwritten) is the reduce
+ * of [0, min(2^min(r,64), cap)), equal to hlf_enumerate_reduce over that
+ * window, with r read on the device from the factorisation (all zero if the
+ * factorisation failed; the fault is reported by hlf_get_status). Work on
+ * `stream` first waits for the factor kernel's stream. The grid is sized for
+ * cap, so a cap far above 2^r leaves threads idle.
+ */
+hlf_status hlf_enumerate_reduce_upto(hlf_handle* h, uint64_t cap, hlf_reduce* red_dev, void* stream);
+
+/*
  * Stage 2, materialised densely: the same solutions as hlf_enumerate_store,
  * n bits each, back to back. Solution z(offset + t) occupies bits
  * [t*n, (t+1)*n) of the stream at out_dev, where stream bit b is bit b % 64
@@ -264,26 +275,39 @@ hlf_status hlf_many_destroy(hlf_many* m);
 
 /* ------------------------------------------------------------------ batched
  * Many independent matrices (the batched workload: thousands of grids of
- * uneven n) factored (stage 1) and reduced (stage 2) in ONE persistent
- * kernel launch. CTAs pull work items from an on-device queue: first one
- * factorisation per matrix, then fixed-size chunks of each matrix's index
- * space; a chunk waits, with a bounded number of polls, for its matrix's
- * factorisation. The paper has no batched mode: this is the same arithmetic
- * as hlf_factor + hlf_enumerate_reduce, scheduled across matrices.
+ * uneven n) factored (stage 1) and enumerated (stage 2) by persistent kernel
+ * launches. CTAs pull work items from an on-device queue: one factorisation
+ * per matrix, and fixed-size chunks of each matrix's index space; in the
+ * fused launch a chunk waits, with a bounded number of polls, for its
+ * matrix's factorisation. The paper has no batched mode: this is the same
+ * arithmetic as hlf_factor + hlf_enumerate_reduce / hlf_enumerate_store,
+ * scheduled across matrices. Each item is worked on by one CTA of 2, 4 or 8
+ * warps (hlf_batch_set_tiles).
+ *
+ * Two forms:
+ *   hlf_factor_batched, then hlf_enumerate_batched: the ragged batch is
+ *     given as ONE packed buffer and an offsets table of count + 1 entries;
+ *     the factorisations stay resident in the plan between the calls, so one
+ *     factorisation can be enumerated several times (reduced, then stored);
+ *   hlf_batch_factor_reduce: factor and reduce in one launch (word offset
+ *     and n per matrix), the shape the batched benchmark times.
  */
 
-#define HLF_BATCH_MAX_N 256 /* largest n in a batch (one CTA of 256 threads per factorisation) */
+#define HLF_BATCH_MAX_N 256 /* largest n in a batch */
 
 typedef struct hlf_batch hlf_batch;
 
 /* Creates a batch plan with device workspace for up to max_instances
- * matrices (per matrix: a 66 x 4-word table, status, rank, a ready flag;
+ * matrices (per matrix: a 66 x 4-word table, status, rank, n, a ready flag;
  * about 2.1 KiB). The plan is bound to the current device. */
 hlf_status hlf_batch_create(int32_t max_instances, hlf_batch** b);
 
-/* Launch shape chosen by an autotuner: CTAs per SM (0 = as many as fit) and
- * solutions per work item (a power of two >= 256). */
-hlf_status hlf_batch_set_tiles(hlf_batch* b, int32_t ctas_per_sm, uint64_t chunk);
+/* Launch shape, chosen by the autotuner: warps per work item (2, 4 or 8: the
+ * CTA size; a CTA of 32w threads holds 8/w rows of a matrix per thread),
+ * CTAs per SM (0 = as many as fit) and solutions per chunk item (a power of
+ * two >= 256). Default: 8 warps, as many CTAs as fit, 2^16. Results do not
+ * depend on the shape. */
+hlf_status hlf_batch_set_tiles(hlf_batch* b, int32_t warps_per_item, int32_t ctas_per_sm, uint64_t chunk);
 
 /* Bound on the polls a chunk makes while waiting for its matrix (default
  * 2^23 polls of >= 128 ns); past it the chunk is skipped and the batch status
@@ -297,9 +321,50 @@ hlf_status hlf_batch_set_spin_limit(hlf_batch* b, uint32_t polls);
 hlf_status hlf_batch_set_debug(hlf_batch* b, uint32_t flags);
 
 /*
- * Factor and reduce `count` matrices in one launch (plus three memsets), all
+ * Stage 1 of `count` matrices in one launch (Section 2, steps (1)-(4), per
+ * matrix), enqueued on `stream` with no host synchronisation.
+ *   A_dev        device, all matrices' rows back to back: matrix b is the
+ *                words [offsets_dev[b], offsets_dev[b+1]) of A_dev, [n_b][W_b]
+ *                with W_b = ceil(n_b / 64). n_b is read from the size
+ *                (n * ceil(n/64) words determines n); a size that fits no
+ *                n in [1, HLF_BATCH_MAX_N] fails that matrix alone with
+ *                HLF_ERR_SIZE.
+ *   offsets_dev  device int64[count + 1], nondecreasing, offsets_dev[0] the
+ *                first matrix's word offset.
+ *   r_dev        device int32[count]: the rank, or -(hlf_status) if that
+ *                matrix failed (not symmetric, padding, size).
+ * The factorisations stay in the plan until its next factor or fused call.
+ * Host-side errors: HLF_ERR_ARG (bad pointers, count > max_instances, plan
+ * made on another device).
+ */
+hlf_status hlf_factor_batched(hlf_batch* b, const uint64_t* A_dev, const int64_t* offsets_dev, int32_t count,
+                              int32_t* r_dev, void* stream);
+
+/*
+ * Stage 2 of the matrices of the plan's last hlf_factor_batched (or
+ * hlf_batch_factor_reduce) call, in one launch: for each matrix b with rank
+ * r_b, the solutions z(i), i < total_b = min(2^min(r_b, 64), cap), in the
+ * Gray order of the conventions above. Exactly one of:
+ *   red_dev  device hlf_reduce[count], overwritten with each matrix's
+ *            (count, hash sum, XOR-fold) over [0, total_b);
+ *   out_dev + out_offsets_dev  device: matrix b writes z(i) for
+ *            i < min(total_b, room_b) to out_dev + out_offsets_dev[b] + i*W_b,
+ *            W_b words each, where room_b = (out_offsets_dev[b+1] -
+ *            out_offsets_dev[b]) / W_b (an int64[count + 1] offsets table of
+ *            the caller's output buffer, 8-byte aligned words).
+ * A matrix whose factorisation failed is skipped (its reduce reads 0).
+ * Host-side errors: HLF_ERR_ARG (no factorisation in the plan, both or
+ * neither output given), HLF_ERR_RANGE (cap needs more than 2^20 chunks).
+ */
+hlf_status hlf_enumerate_batched(hlf_batch* b, uint64_t cap, hlf_reduce* red_dev, uint64_t* out_dev,
+                                 const int64_t* out_offsets_dev, void* stream);
+
+/*
+ * Factor and reduce `count` matrices in ONE launch (plus three memsets), all
  * enqueued on `stream` with no host synchronisation (so it can be captured in
- * a CUDA graph).
+ * a CUDA graph). The same results as hlf_factor_batched followed by
+ * hlf_enumerate_batched with red_dev; the input is described per matrix
+ * instead of by an offsets table:
  *   A_dev        device, the matrices' rows back to back: matrix b is
  *                [n_b][W_b] words starting at word word_off_dev[b].
  *   word_off_dev device int64[count]; n_dev device int32[count], each n_b in
@@ -308,6 +373,7 @@ hlf_status hlf_batch_set_debug(hlf_batch* b, uint32_t flags);
  *   r_dev        device int32[count]: the rank, or -(hlf_status) if that
  *                matrix failed (not symmetric, padding, size).
  *   red_dev      device hlf_reduce[count], overwritten.
+ * The factorisations stay in the plan, as after hlf_factor_batched.
  * Host-side errors: HLF_ERR_ARG (bad pointers, count > max_instances, plan
  * made on another device), HLF_ERR_RANGE (too many work items).
  */
@@ -337,8 +403,8 @@ hlf_status hlf_batch_destroy(hlf_batch* b);
  * cudaFree or any allocating routine.
  *
  * Arguments, layout and results are those of hlf_batch_factor_reduce with the
- * default launch shape (CTAs per SM: as many as fit; 2^16 solutions per work
- * item; 2^23 polls per wait). count > HLF_BATCH_NOALLOC_MAX returns
+ * default launch shape (8 warps per work item; CTAs per SM: as many as fit;
+ * 2^16 solutions per work item; 2^23 polls per wait). count > HLF_BATCH_NOALLOC_MAX returns
  * HLF_ERR_SIZE and enqueues nothing. A bounded wait that runs out cannot be
  * reported separately here; it shows as red_dev[b].count below
  * min(2^r_b, cap), which a caller checks to detect it.

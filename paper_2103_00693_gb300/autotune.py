@@ -1,7 +1,8 @@
 """Autotuner for the batched launch shape.
 
-The knobs are the persistent grid's CTAs per SM and the solutions per work
-item (chunk). Each candidate runs the real batch a few times, timed with CUDA
+The knobs are the warps that work on each queue item (the CTA size: 2, 4
+or 8 warps per factorisation and per chunk), the persistent grid's CTAs per
+SM and the solutions per chunk item. Each candidate runs the real batch a few times, timed with CUDA
 events on the launching stream; the fastest is kept. Results are cached per
 (GPU name, batch signature) in a JSON file next to the built library, so a
 later process with the same kind of batch skips the search.
@@ -19,8 +20,9 @@ import numpy as np
 
 from . import build as _build
 
-CTAS_PER_SM = (1, 2, 3, 0)          # 0 = as many as fit
-CHUNKS = (1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)
+WARPS = (2, 4, 8)                   # warps per work item (CTA size / 32)
+CTAS_PER_SM = (1, 2, 4, 0)          # 0 = as many as fit
+CHUNKS = (1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)
 CACHE = os.path.join(_build.OUT_DIR, "autotune.json")
 
 
@@ -70,22 +72,23 @@ def time_batch(batch, cap: int, reps: int = 3) -> float:
 
 
 def autotune(batch, cap: int, reps: int = 3, use_cache: bool = True) -> dict:
-    """Pick (ctas_per_sm, chunk) for this batch; set it on the batch and
-    return {"tiles": [cps, chunk], "ms": best, "table": [...], "cached": bool}."""
+    """Pick (warps_per_item, ctas_per_sm, chunk) for this batch; set it on
+    the batch and return {"tiles": [warps, cps, chunk], "ms": best,
+    "table": [...], "cached": bool}."""
     key = f"{_gpu_name()}|{signature(batch.Ws, cap)}"
     cache = _load_cache() if use_cache else {}
-    if key in cache:
-        cps, chunk = cache[key]["tiles"]
-        batch.set_tiles(cps, chunk)
+    if key in cache and len(cache[key].get("tiles", ())) == 3:
+        batch.set_tiles(*cache[key]["tiles"])
         return dict(cache[key], cached=True)
     table = []
-    for cps in CTAS_PER_SM:
-        for chunk in CHUNKS:
-            batch.set_tiles(cps, chunk)
-            table.append((cps, chunk, time_batch(batch, cap, reps)))
-    cps, chunk, ms = min(table, key=lambda t: t[2])
-    batch.set_tiles(cps, chunk)
-    entry = {"tiles": [cps, chunk], "ms": ms, "table": [list(t) for t in table]}
+    for warps in WARPS:
+        for cps in CTAS_PER_SM:
+            for chunk in CHUNKS:
+                batch.set_tiles(warps, cps, chunk)
+                table.append((warps, cps, chunk, time_batch(batch, cap, reps)))
+    warps, cps, chunk, ms = min(table, key=lambda t: t[3])
+    batch.set_tiles(warps, cps, chunk)
+    entry = {"tiles": [warps, cps, chunk], "ms": ms, "table": [list(t) for t in table]}
     if use_cache:
         cache = _load_cache()
         cache[key] = entry

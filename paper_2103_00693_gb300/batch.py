@@ -1,6 +1,7 @@
 """Batched factorisation + reduction of many matrices in one persistent
-launch (hlf_batch_* in include/hlf.h), with CUDA-graph capture and the plain
-one-launch-per-matrix path it is compared with.
+launch (hlf_batch_*, hlf_factor_batched, hlf_enumerate_batched in
+include/hlf.h), with CUDA-graph capture and the plain one-launch-per-matrix
+path it is compared with.
 
 Packing the matrices into one device buffer (rows back to back, a word
 offset and n per matrix) is argument marshalling; all solver work runs in
@@ -26,26 +27,40 @@ class Batch:
             raise ValueError(f"batched matrices need 1 <= n <= {hlf.BATCH_MAX_N}")
         self.Ws = (self.ns + 63) // 64
         sizes = self.ns.astype(np.int64) * self.Ws
-        self.word_off = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)  # [count + 1]
+        self.word_off = self.offsets[:-1].copy()
         packed = np.concatenate([hlf.pack_rows(A).ravel() for A in mats]) if mats else np.zeros(0, np.uint64)
         self.A_dev = torch.from_numpy(packed.view(np.int64)).to(device)
         self.off_dev = torch.from_numpy(self.word_off).to(device)
+        self.offsets_dev = torch.from_numpy(self.offsets).to(device)
         self.n_dev = torch.from_numpy(self.ns).to(device)
         self.r_dev = torch.empty(self.count, dtype=torch.int32, device=device)
         self.red_dev = torch.empty((self.count, hlf.REDUCE_WORDS), dtype=torch.int64, device=device)
         self.plan = hlf.hlf_batch_create(max(self.count, 1))
-        self.tiles = (0, 1 << 16)
+        self.tiles = (8, 0, 1 << 16)
         self.graph = None
 
-    def set_tiles(self, ctas_per_sm: int, chunk: int):
-        hlf.hlf_batch_set_tiles(self.plan, ctas_per_sm, chunk)
-        self.tiles = (ctas_per_sm, chunk)
+    def set_tiles(self, warps_per_item: int, ctas_per_sm: int, chunk: int):
+        hlf.hlf_batch_set_tiles(self.plan, warps_per_item, ctas_per_sm, chunk)
+        self.tiles = (warps_per_item, ctas_per_sm, chunk)
 
     def run(self, cap: int, stream=None):
-        """Enqueue one launch: factor every matrix, reduce solutions
+        """Enqueue one fused launch: factor every matrix, reduce solutions
         [0, min(2^r, cap)) of each."""
         hlf.hlf_batch_factor_reduce(self.plan, self.A_dev, self.off_dev, self.n_dev, self.count, cap,
                                     self.r_dev, self.red_dev, stream)
+
+    def factor(self, stream=None):
+        """Stage 1 of every matrix (hlf_factor_batched, offsets table [count + 1])."""
+        hlf.hlf_factor_batched(self.plan, self.A_dev, self.offsets_dev, self.count, self.r_dev, stream)
+
+    def reduce(self, cap: int, stream=None):
+        """Stage 2 reduce of the factored matrices into red_dev."""
+        hlf.hlf_enumerate_batched(self.plan, cap, red_dev=self.red_dev, stream=stream)
+
+    def store(self, cap: int, out_dev, out_offsets_dev, stream=None):
+        """Stage 2 store of the factored matrices into out_dev at out_offsets_dev."""
+        hlf.hlf_enumerate_batched(self.plan, cap, out_dev=out_dev, out_offsets_dev=out_offsets_dev, stream=stream)
 
     def capture(self, cap: int):
         """Capture run(cap) into a CUDA graph; replay() re-runs it."""
@@ -86,30 +101,51 @@ class Batch:
             pass
 
 
-def per_instance(mats: list[np.ndarray], cap: int, device: str = "cuda"):
-    """The plain path: for each matrix, hlf_factor then hlf_enumerate_reduce of
-    [0, min(2^r, cap)) (one factor launch and one reduce launch per matrix; the
-    reduce needs r on the host, so each matrix waits for its factorisation).
-    Returns (ranks, reduce tensor [count, 18])."""
-    import torch
+class PlainPath:
+    """The plain path the batched launch is compared with: for each matrix,
+    one factor launch (hlf_factor) and one reduce launch of [0, min(2^r, cap))
+    (hlf_enumerate_reduce_upto, which reads r on the device), all enqueued on
+    one stream with no host wait; the matrices are staged on the device once,
+    before any timing."""
 
-    count = len(mats)
-    red = torch.empty((count, hlf.REDUCE_WORDS), dtype=torch.int64, device=device)
-    ranks = np.zeros(count, dtype=np.int32)
-    packed = [torch.from_numpy(hlf.pack_rows(A).view(np.int64)).to(device) for A in mats]
-    for b, A in enumerate(mats):
-        h = hlf.hlf_factor(packed[b], A.shape[0])
-        r = hlf.hlf_get_rank(h)
-        ranks[b] = r
-        total = min(1 << min(r, 64), cap)
-        hlf.hlf_enumerate_reduce(h, 0, total, red[b])
-        hlf.hlf_destroy(h)
-    return ranks, red
+    def __init__(self, mats: list[np.ndarray], device: str = "cuda"):
+        import torch
+
+        self.count = len(mats)
+        self.ns = [A.shape[0] for A in mats]
+        packed = np.concatenate([hlf.pack_rows(A).ravel() for A in mats]) if mats else np.zeros(0, np.uint64)
+        self.A_dev = torch.from_numpy(packed.view(np.int64)).to(device)
+        self.views = []
+        at = 0
+        for n in self.ns:
+            W = hlf.words(n)
+            self.views.append(self.A_dev[at: at + n * W].view(n, W))
+            at += n * W
+        self.red_dev = torch.empty((self.count, hlf.REDUCE_WORDS), dtype=torch.int64, device=device)
+
+    def run(self, cap: int, stream=None, ranks: bool = False):
+        """Enqueue every matrix's two launches; with ranks=True also wait for
+        and return each rank (for tests; the timed path does not)."""
+        out = np.zeros(self.count, dtype=np.int32) if ranks else None
+        for b in range(self.count):
+            h = hlf.hlf_factor(self.views[b], self.ns[b], stream)
+            hlf.hlf_enumerate_reduce_upto(h, cap, self.red_dev[b], stream)
+            if ranks:
+                out[b] = hlf.hlf_get_rank(h)
+            hlf.hlf_destroy(h)
+        return out
+
+
+def per_instance(mats: list[np.ndarray], cap: int, device: str = "cuda"):
+    """The plain path run once: (ranks, reduce tensor [count, 18])."""
+    p = PlainPath(mats, device)
+    ranks = p.run(cap, ranks=True)
+    return ranks, p.red_dev
 
 
 def main(argv=None):
     """Run the batched workload (or its first `--count` grids) once and
-    print launch time and throughput; `--tiles CTAS CHUNK` skips the
+    print launch time and throughput; `--tiles WARPS CTAS CHUNK` skips the
     autotuner."""
     import argparse
     import time
@@ -122,13 +158,13 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--cap-log2", type=int, default=wl.BATCH_CAP_LOG2)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--tiles", type=int, nargs=2, default=None)
+    ap.add_argument("--tiles", type=int, nargs=3, default=None)
     a = ap.parse_args(argv)
     mats = wl.batch()[: a.count]
     cap = 1 << a.cap_log2
     B = Batch(mats)
     if a.tiles:
-        B.set_tiles(a.tiles[0], a.tiles[1])
+        B.set_tiles(a.tiles[0], a.tiles[1], a.tiles[2])
     else:
         from . import autotune
 

@@ -38,13 +38,14 @@
 
 namespace hlf {
 
-template <int W, int MAXN>
+// NW: the most warps a CTA running factor_block may have (32 by default).
+template <int W, int MAXN, int NW = 32>
 struct FactorSmem {
-    int first[2][32];        // per warp: its lowest candidate's key for the column (by column parity)
-    uint64_t crow[2][32][W];  // and that row's words
+    int first[2][NW];        // per warp: its lowest candidate's key for the column (by column parity)
+    uint64_t crow[2][NW][W];  // and that row's words
     int pivcol[MAXN];
     uint32_t pivmask[MAXN / 32];
-    uint64_t x[32][W];
+    uint64_t x[NW][W];
     uint64_t z0[W];
     int err;
 };
@@ -85,25 +86,27 @@ __device__ __forceinline__ void transpose64_warp(uint64_t& x0, uint64_t& x1, int
 template <int W>
 constexpr int basis_stride() { return W | 1; }
 
-template <int W, int MAXN>
+template <int W, int MAXN, int NW = 32>
 constexpr size_t factor_smem_bytes(int n)
 {
-    return sizeof(FactorSmem<W, MAXN>) + (size_t)n * basis_stride<W>() * sizeof(uint64_t);
+    return sizeof(FactorSmem<W, MAXN, NW>) + (size_t)n * basis_stride<W>() * sizeof(uint64_t);
 }
 
 // Factor the n x n matrix A ([n][W] words, global) with the whole CTA.
 // Thread t owns the R rows t, t + blockDim.x, ... in registers. Requires
-// R * blockDim.x >= n, blockDim.x a multiple of 32, n <= MAXN. `smem` points
-// to factor_smem_bytes<W, MAXN>(n) bytes of shared memory. Writes o.table
+// R * blockDim.x >= n, blockDim.x a multiple of 32 and at most 32 * NW,
+// n <= MAXN. `smem` points to factor_smem_bytes<W, MAXN, NW>(n) bytes of
+// shared memory. Writes o.table
 // (always), o.basis and o.piv (when non-null) and o.info[0] = status,
 // o.info[1] = r (or -1 on a fault). Returns r, or -1.
-template <int W, int R, int MAXN>
+template <int W, int R, int MAXN, int NW = 32>
 __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorOut& o, unsigned char* smem)
 {
     constexpr int kNone = 0x7fffffff;
-    FactorSmem<W, MAXN>& sm = *reinterpret_cast<FactorSmem<W, MAXN>*>(smem);
+    using Smem = FactorSmem<W, MAXN, NW>;
+    Smem& sm = *reinterpret_cast<Smem*>(smem);
     constexpr int SW = basis_stride<W>();
-    uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem + sizeof(FactorSmem<W, MAXN>));  // [n][SW]
+    uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem + sizeof(Smem));  // [n][SW]
 
     const int tid = threadIdx.x;
     const int bs = blockDim.x;

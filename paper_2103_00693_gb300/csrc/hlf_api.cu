@@ -458,6 +458,18 @@ hlf_status hlf_enumerate_store_upto(hlf_handle* h, uint64_t cap, uint64_t* out_d
     return after_launch(h, hlf::launch_store_upto(enum_table(h), h->W, h->info_dev, cap, out_dev, s), s);
 }
 
+hlf_status hlf_enumerate_reduce_upto(hlf_handle* h, uint64_t cap, hlf_reduce* red_dev, void* stream)
+{
+    if (!h || !red_dev) return HLF_ERR_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return HLF_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamWaitEvent(s, h->factored, 0) != cudaSuccess) return HLF_ERR_CUDA;
+    if (cudaMemsetAsync(red_dev, 0, sizeof(hlf_reduce), s) != cudaSuccess) return HLF_ERR_CUDA;
+    if (cap == 0) return after_launch(h, HLF_OK, s);
+    return after_launch(h, hlf::launch_reduce_upto(enum_table(h), h->W, h->info_dev, cap, red_dev, s), s);
+}
+
 hlf_status hlf_enumerate_store_dense(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev,
                                      void* stream)
 {

@@ -1,5 +1,5 @@
-// Launcher of the small-instance store (upto.cu): every solution of a
-// handle up to a cap, with the rank read on the device.
+// Launchers of the small-instance store and reduce (upto.cu): every solution
+// of a handle up to a cap, with the rank read on the device.
 #pragma once
 
 #include "hlf_internal.cuh"
@@ -10,5 +10,10 @@ namespace hlf {
 // kernel left it (nothing is written when r < 0). out: 8-byte aligned.
 hlf_status launch_store_upto(const uint64_t* table, int W, const int32_t* info, uint64_t cap, uint64_t* out,
                              cudaStream_t s);
+
+// *out (zeroed by the caller) += the reduce of [0, min(2^r, cap)); nothing is
+// added when r < 0.
+hlf_status launch_reduce_upto(const uint64_t* table, int W, const int32_t* info, uint64_t cap, hlf_reduce* out,
+                              cudaStream_t s);
 
 }  // namespace hlf

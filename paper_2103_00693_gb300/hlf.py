@@ -49,6 +49,7 @@ SIGNATURES = {
     "hlf_get_status": (ctypes.c_int, [_vp]),
     "hlf_enumerate_store": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_store_upto": (ctypes.c_int, [_vp, _u64, _vp, _vp]),
+    "hlf_enumerate_reduce_upto": (ctypes.c_int, [_vp, _u64, _vp, _vp]),
     "hlf_enumerate_store_dense": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_reduce": (ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     "hlf_enumerate_reduce_chunks": (ctypes.c_int, [_vp, _u64, _u64, _u64, _vp, _vp]),
@@ -59,7 +60,9 @@ SIGNATURES = {
     "hlf_enumerate_store_many": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _i32, _vp]),
     "hlf_many_destroy": (ctypes.c_int, [_vp]),
     "hlf_batch_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp)]),
-    "hlf_batch_set_tiles": (ctypes.c_int, [_vp, _i32, _u64]),
+    "hlf_batch_set_tiles": (ctypes.c_int, [_vp, _i32, _i32, _u64]),
+    "hlf_factor_batched": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "hlf_enumerate_batched": (ctypes.c_int, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "hlf_batch_set_spin_limit": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "hlf_batch_factor_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _u64, _vp, _vp, _vp]),
     "hlf_batch_set_debug": (ctypes.c_int, [_vp, ctypes.c_uint32]),
@@ -233,6 +236,13 @@ def hlf_enumerate_store_upto(h: int, cap: int, out_dev, stream=None):
                                            _stream_ptr(stream)), "hlf_enumerate_store_upto")
 
 
+def hlf_enumerate_reduce_upto(h: int, cap: int, red_dev, stream=None):
+    """Reduce of [0, min(2^r, cap)) into red_dev [18] with r read on the
+    device: no host wait after hlf_factor."""
+    _check(load().hlf_enumerate_reduce_upto(h, cap, _ptr(red_dev), _stream_ptr(stream)),
+           "hlf_enumerate_reduce_upto")
+
+
 def hlf_enumerate_store_dense(h: int, offset: int, count: int, out_dev, stream=None):
     _check(load().hlf_enumerate_store_dense(h, offset, count, _ptr(out_dev) if out_dev is not None else None,
                                             _stream_ptr(stream)), "hlf_enumerate_store_dense")
@@ -297,8 +307,24 @@ def hlf_batch_create(max_instances: int) -> int:
     return b.value
 
 
-def hlf_batch_set_tiles(b: int, ctas_per_sm: int, chunk: int):
-    _check(load().hlf_batch_set_tiles(b, ctas_per_sm, chunk), "hlf_batch_set_tiles")
+def hlf_batch_set_tiles(b: int, warps_per_item: int, ctas_per_sm: int, chunk: int):
+    _check(load().hlf_batch_set_tiles(b, warps_per_item, ctas_per_sm, chunk), "hlf_batch_set_tiles")
+
+
+def hlf_factor_batched(b: int, A_dev, offsets_dev, count: int, r_dev, stream=None):
+    """Stage 1 of `count` matrices packed back to back in A_dev, matrix b in
+    words [offsets_dev[b], offsets_dev[b+1]) (offsets: int64 [count + 1])."""
+    _check(load().hlf_factor_batched(b, _ptr(A_dev), _ptr(offsets_dev), count, _ptr(r_dev), _stream_ptr(stream)),
+           "hlf_factor_batched")
+
+
+def hlf_enumerate_batched(b: int, cap: int, red_dev=None, out_dev=None, out_offsets_dev=None, stream=None):
+    """Stage 2 of the plan's factored matrices: reduce into red_dev [count,
+    18], or store into out_dev at out_offsets_dev (int64 [count + 1])."""
+    _check(load().hlf_enumerate_batched(b, cap, _ptr(red_dev) if red_dev is not None else None,
+                                        _ptr(out_dev) if out_dev is not None else None,
+                                        _ptr(out_offsets_dev) if out_offsets_dev is not None else None,
+                                        _stream_ptr(stream)), "hlf_enumerate_batched")
 
 
 def hlf_batch_set_spin_limit(b: int, polls: int):

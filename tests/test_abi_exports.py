@@ -121,3 +121,13 @@ def test_package_reexports_every_entry_point():
     status-string and device-count helpers included)."""
     missing = [name for name in hlf.SIGNATURES if not hasattr(hlf, name)]
     assert not missing, missing
+
+
+def test_batched_and_upto_argument_checks(lib):
+    """The batched calls and the device-rank reduce check their arguments on
+    the host before touching the GPU."""
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.hlf_factor_batched(None, fake, fake, 4, fake, None) == 1
+    assert lib.hlf_enumerate_batched(None, 16, fake, None, None, None) == 1
+    assert lib.hlf_enumerate_reduce_upto(None, 16, fake, None) == 1
+    assert lib.hlf_batch_set_tiles(None, 8, 0, 256) == 1

@@ -1,7 +1,10 @@
-"""The batched persistent launch against the oracle and against the plain
+"""The batched persistent launches against the oracle and against the plain
 one-matrix-per-launch path: every matrix's result is the same alone and in
-the mix (exact), under graph replay, and for bad matrices mixed in; bounded
-waits that run out report HLF_ERR_TIMEOUT and leave the context usable."""
+the mix (exact), in the fused launch and in the two separate calls
+(hlf_factor_batched with an offsets table, then hlf_enumerate_batched
+reducing or storing), under every launch shape, under graph replay, and for
+bad matrices mixed in; bounded waits that run out report HLF_ERR_TIMEOUT and
+leave the context usable."""
 
 import numpy as np
 import pytest
@@ -69,8 +72,9 @@ def test_batch_tiles_do_not_change_results(cuda_ok):
     cap = 1 << 16
     B = Batch(mats)
     ref = None
-    for cps, chunk in ((0, 1 << 16), (1, 1 << 13), (2, 1 << 17), (3, 256)):
-        B.set_tiles(cps, chunk)
+    for warps, cps, chunk in ((8, 0, 1 << 16), (8, 1, 1 << 13), (4, 2, 1 << 17), (2, 3, 256), (2, 0, 1 << 14),
+                              (4, 0, 1 << 15)):
+        B.set_tiles(warps, cps, chunk)
         B.run(cap)
         assert B.status() == 0
         got = B.red_dev.cpu().numpy().copy()
@@ -139,3 +143,114 @@ def test_batch4096_alone_and_in_the_mix(cuda_ok):
         rr, c, h, f = _oracle_expect(mats[b], cap)
         assert r[b] == rr and (red[b].count, red[b].hsum) == (c, h) and np.array_equal(red[b].xor_fold, f)
     B.close()
+
+
+@pytest.mark.parametrize("warps", [2, 4, 8])
+def test_split_calls_equal_fused_and_oracle(cuda_ok, warps):
+    """hlf_factor_batched (n from the offsets table) + hlf_enumerate_batched
+    reduce equal the fused launch and the oracle for every matrix of the mix
+    (n = 1 .. 256, W = 1 .. 4, rank 0 .. n)."""
+    mats = _mix()
+    cap = 1 << 13
+    B = Batch(mats)
+    B.set_tiles(warps, 0, 1 << 12)
+    B.run(cap)
+    assert B.status() == 0
+    fused_r = B.r_dev.cpu().numpy().copy()
+    fused = B.red_dev.cpu().numpy().copy()
+    B.r_dev.fill_(-99)
+    B.red_dev.fill_(-1)
+    B.factor()
+    B.reduce(cap)
+    assert B.status() == 0
+    assert np.array_equal(B.r_dev.cpu().numpy(), fused_r)
+    assert np.array_equal(B.red_dev.cpu().numpy(), fused)
+    r, red = B.results()
+    for b in range(0, len(mats), 3):
+        rr, c, h, f = _oracle_expect(mats[b], cap)
+        assert r[b] == rr and (red[b].count, red[b].hsum) == (c, h) and np.array_equal(red[b].xor_fold, f), b
+    B.close()
+
+
+@pytest.mark.parametrize("warps", [2, 8])
+def test_batched_store_against_oracle(cuda_ok, warps):
+    """hlf_enumerate_batched storing: matrix b writes z(i), i < min(2^r_b,
+    cap, room_b), at its offset, W_b words each; nothing past that is
+    touched. A ragged cap (not a multiple of 32), rooms smaller than the cap
+    and an empty room are included; the same factorisations are reduced
+    first and stored after."""
+    import torch
+
+    mats = _mix()
+    cap = 1000
+    B = Batch(mats)
+    B.set_tiles(warps, 0, 256)
+    B.factor()
+    B.reduce(cap)
+    want_red = B.red_dev.cpu().numpy().copy()
+    Ws = B.Ws.astype(np.int64)
+    rooms = np.full(len(mats), cap, dtype=np.int64)
+    rooms[1], rooms[4], rooms[7], rooms[-1] = 37, 0, 100, 999
+    spare = np.full(len(mats), 5, dtype=np.int64)  # extra words: a room may exceed what is written
+    spare[4] = 0  # instance 4 gets an empty region
+    sizes = rooms * Ws + spare
+    table = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)  # [count + 1]
+    out = torch.full((int(table[-1]),), -1, dtype=torch.int64, device="cuda")
+    B.store(cap, out, torch.from_numpy(table).cuda())
+    assert B.status() == 0
+    got = out.cpu().numpy().view(np.uint64)
+    starts = table
+    for b, A in enumerate(mats):
+        F = oc.factor(A)
+        room_b = (int(table[b + 1]) - int(table[b])) // int(Ws[b])
+        k = min(1 << min(F.r, 64), cap, room_b)
+        if b == 4:
+            assert k == 0
+        if k:
+            blk = got[starts[b]: starts[b] + k * Ws[b]].reshape(k, Ws[b])
+            assert np.array_equal(blk, oc.window(F, 0, k)), b
+        rest = got[starts[b] + k * Ws[b]: starts[b + 1]]
+        assert np.all(rest == np.uint64(0xFFFFFFFFFFFFFFFF)), b
+    # the store left the factorisations and the earlier reduce intact
+    B.reduce(cap)
+    assert np.array_equal(B.red_dev.cpu().numpy(), want_red)
+    B.close()
+
+
+def test_factor_batched_bad_sizes_fail_alone(cuda_ok):
+    """A matrix whose word count is n * ceil(n/64) for no n <= 256 fails
+    alone with HLF_ERR_SIZE; the others are exact."""
+    import torch
+
+    mats = synth.batch_instances(5, 4, 8, 0.5, 12)
+    packed = [hlf.pack_rows(A).ravel() for A in mats]
+    junk = np.zeros(65, dtype=np.uint64)  # 65 words: no n has that size
+    parts = packed[:2] + [junk] + packed[2:]
+    sizes = [len(p) for p in parts]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    A_dev = torch.from_numpy(np.concatenate(parts).view(np.int64)).cuda()
+    plan = hlf.hlf_batch_create(len(parts))
+    r = torch.empty(len(parts), dtype=torch.int32, device="cuda")
+    red = torch.empty((len(parts), hlf.REDUCE_WORDS), dtype=torch.int64, device="cuda")
+    hlf.hlf_factor_batched(plan, A_dev, torch.from_numpy(offs).cuda(), len(parts), r)
+    hlf.hlf_enumerate_batched(plan, 1 << 10, red_dev=red)
+    assert hlf.hlf_batch_get_status(plan) == 0
+    rr = r.cpu().numpy()
+    assert rr[2] == -hlf.STATUS_CODES["HLF_ERR_SIZE"]
+    assert not red[2].cpu().numpy().any()
+    for b, A in zip([0, 1, 3, 4, 5, 6], mats):
+        want = _oracle_expect(A, 1 << 10)
+        got = hlf.ReduceResult.from_words(red[b].cpu().numpy(), hlf.words(A.shape[0]))
+        assert rr[b] == want[0] and (got.count, got.hsum) == want[1:3], b
+    hlf.hlf_batch_destroy(plan)
+
+
+def test_enumerate_batched_needs_a_factorisation(cuda_ok):
+    import torch
+
+    plan = hlf.hlf_batch_create(4)
+    red = torch.empty((4, hlf.REDUCE_WORDS), dtype=torch.int64, device="cuda")
+    with pytest.raises(hlf.HlfError) as e:
+        hlf.hlf_enumerate_batched(plan, 16, red_dev=red)
+    assert e.value.status == hlf.STATUS_CODES["HLF_ERR_ARG"]
+    hlf.hlf_batch_destroy(plan)

@@ -132,3 +132,41 @@ def test_many_handles_recycle_status_slots(cuda_ok):
         if k % 500 == 0:
             assert np.array_equal(out[:1 << F.r].cpu().numpy().view(np.uint64), want)
         hlf.hlf_destroy(h)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_reduce_upto_equals_reduce(cuda_ok, order):
+    """hlf_enumerate_reduce_upto (r read on the device) equals
+    hlf_enumerate_reduce over [0, min(2^r, cap)) in both orders, for caps
+    below, at and above 2^r; a failed factorisation reduces to zeros and its
+    fault stays in the status word."""
+    import torch
+
+    import paper_2103_00693_gb300 as hlf
+
+    for A in (synth.grid_instance(3, 0.5, 5), synth.grid_instance(5, 0.5, 2), synth.grid_instance(9, 0.5, 1),
+              synth.random_symmetric(150, 0.5, 3), np.zeros((7, 7), dtype=np.uint8)):
+        F = oc.factor(A)
+        G = hlf.Factorization.from_dense(A)
+        hlf.hlf_set_order(G.h, order)
+        space = 1 << min(F.r, 64)
+        for cap in (c for c in (1, 1000, space, 3 * space + 5, 1 << 21) if c < 1 << 64):
+            red = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, device="cuda")
+            hlf.hlf_enumerate_reduce_upto(G.h, cap, red)
+            want = G.reduce(0, min(space, cap)).cpu().numpy()
+            assert np.array_equal(red.cpu().numpy(), want), (A.shape[0], cap)
+        if order == 0:  # the paper order's windows are checked through hlf_enumerate_reduce's own tests
+            c, h, f = oc.reduce(F, 0, min(space, 1 << 21))
+            got = hlf.ReduceResult.from_words(red.cpu().numpy(), F.W)
+            assert (got.count, got.hsum) == (c, h) and np.array_equal(got.xor_fold, f)
+        G.close()
+    bad = synth.grid_instance(4, 0.5, 3)
+    bad[0, 5] ^= 1
+    Ab = torch.from_numpy(hlf.pack_rows(bad).view(np.int64)).cuda()
+    h = hlf.hlf_factor(Ab, bad.shape[0])
+    red = torch.full((hlf.REDUCE_WORDS,), -1, dtype=torch.int64, device="cuda")
+    hlf.hlf_enumerate_reduce_upto(h, 1 << 10, red)
+    torch.cuda.synchronize()
+    assert not red.cpu().numpy().any()
+    assert hlf.hlf_get_status(h) == hlf.STATUS_CODES["HLF_ERR_NOT_SYMMETRIC"]
+    hlf.hlf_destroy(h)

@@ -43,6 +43,10 @@ UNIT = "solutions/s"
 # 64-bit add of the hash 2.
 OPS_PER_SOLUTION_W1 = 20
 ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
+# The histogram walks the table projected onto the field: per solution one
+# 32-bit XOR and one shared-memory atomic add.
+HIST_OPS_PER_SOLUTION = 2
+PROBE_ITERS = 1 << 14
 STORE_LOG2 = 30
 SAMPLE_LOG2 = 20
 SAMPLE_SEED = 99
@@ -457,6 +461,14 @@ def run_next_rows(args, A_dev, n, W, store_n, pk, dev):
     d_ms = timed(lambda: hlf.hlf_enumerate_store_dense(hh, 0, store_n, dense), max(3, args.steps))
     h_ms = timed(lambda: hlf.hlf_enumerate_histogram(hh, 0, hcount, 0, 14, hist), 3)
     hlf.hlf_destroy(hh)
+    # the shared-memory atomic rate of this GPU (the histogram's denominator)
+    psum = torch.empty(1, dtype=torch.int64, device=dev)
+    n_atomics = hlf.hlf_probe_smem_atomics(PROBE_ITERS, psum)
+    p_ms = timed(lambda: hlf.hlf_probe_smem_atomics(PROBE_ITERS, psum), 3)
+    assert int(psum.item()) == n_atomics
+    atomic_peak = n_atomics / (p_ms / 1e3) / 1e12
+    h_rate = hcount / (h_ms / 1e3) / 1e12  # one shared-memory atomic per solution
+    ipk, ipk_basis = int_peak(dev)
     dbytes = hlf.dense_words(store_n, n) * 8
     return {"dense_store": {"solutions": store_n, "bits_per_solution": n, "ms_per_launch": d_ms,
                             "solutions_per_s": store_n / (d_ms / 1e3),
@@ -466,7 +478,16 @@ def run_next_rows(args, A_dev, n, W, store_n, pk, dev):
                                          "kernel": "dense1_kernel<16,1,1>",
                                          "traffic": traffic("dense1_kernel<16,1,1>")}},
             "histogram": {"solutions": hcount, "field": "bits 0..13", "ms_per_launch": h_ms,
-                          "solutions_per_s": hcount / (h_ms / 1e3)}}
+                          "solutions_per_s": hcount / (h_ms / 1e3),
+                          "roofline": {"bound": "smem_atomic", "achieved": h_rate, "peak": atomic_peak,
+                                       "unit": "T atomics/s", "frac": h_rate / atomic_peak,
+                                       "kernel": "hist_interleaved_kernel<true>",
+                                       "peak_basis": f"hlf_probe_smem_atomics: {n_atomics} conflict-free "
+                                                     f"32-bit shared-memory atomics in {p_ms:.3f} ms"},
+                          "roofline_issue": {"bound": "alu", "achieved": HIST_OPS_PER_SOLUTION * h_rate,
+                                             "peak": ipk, "unit": "Tops/s",
+                                             "frac": HIST_OPS_PER_SOLUTION * h_rate / ipk,
+                                             "ops_per_solution": HIST_OPS_PER_SOLUTION, "peak_basis": ipk_basis}}}
 
 
 def run_e2e(args, world, dev, A, r, total, store_n, idx_host, host_bufs=None):

@@ -424,6 +424,19 @@ hlf_status hlf_batch_factor_reduce_noalloc(const uint64_t* A_dev, const int64_t*
                                            const int32_t* n_dev, int32_t count, uint64_t cap, int32_t* r_dev,
                                            hlf_reduce* red_dev, void* stream);
 
+/* ------------------------------------------------------------ measurement
+ * Not part of the method (the paper has no counterpart): a microbenchmark
+ * whose rate is the denominator of the histogram's roofline. One wave of CTAs
+ * in which every thread performs `iters` 32-bit shared-memory atomic adds,
+ * the 32 lanes of a warp on 32 distinct banks (the pattern of
+ * hlf_enumerate_histogram's interleaved walk when its lanes land in distinct
+ * bins). *sum_dev (device, one uint64, overwritten) receives the total of all
+ * counters, which equals *atomics (host), the number of atomics the launch
+ * performs. Time the launch with events on `stream`. iters must be a
+ * positive multiple of 16 (else HLF_ERR_ARG).
+ */
+hlf_status hlf_probe_smem_atomics(uint32_t iters, uint64_t* sum_dev, uint64_t* atomics, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ SIGNATURES = {
     "hlf_batch_get_status": (ctypes.c_int, [_vp]),
     "hlf_batch_destroy": (ctypes.c_int, [_vp]),
     "hlf_batch_factor_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i32, _u64, _vp, _vp, _vp]),
+    "hlf_probe_smem_atomics": (ctypes.c_int, [ctypes.c_uint32, _vp, ctypes.POINTER(_u64), _vp]),
 }
 
 
@@ -474,3 +475,13 @@ class Factorization:
             self.close()
         except Exception:
             pass
+
+
+def hlf_probe_smem_atomics(iters: int, sum_dev, stream=None) -> int:
+    """Launch the shared-memory atomic microbenchmark (a measurement helper,
+    not part of the method); returns the number of atomics it performs, which
+    sum_dev (one int64 on the device) also receives."""
+    n = _u64()
+    _check(load().hlf_probe_smem_atomics(iters, _ptr(sum_dev), ctypes.byref(n), _stream_ptr(stream)),
+           "hlf_probe_smem_atomics")
+    return n.value

@@ -101,3 +101,16 @@ def test_histogram_window_ending_at_2_64(cuda_ok):
             got = G.histogram(off, cnt, lo, nb).cpu().numpy().view(np.uint64)
             assert np.array_equal(got, oc.histogram(F, off, cnt, lo, nb)), (cnt, lo, nb)
     G.close()
+
+
+def test_atomic_probe_counts_every_atomic(cuda_ok):
+    """The shared-memory atomic microbenchmark behind the histogram's
+    roofline performs exactly the atomics it reports."""
+    import torch
+
+    s = torch.empty(1, dtype=torch.int64, device="cuda")
+    for iters in (16, 1 << 10):
+        n = hlf.hlf_probe_smem_atomics(iters, s)
+        assert int(s.item()) == n > 0
+    with pytest.raises(hlf.HlfError):
+        hlf.hlf_probe_smem_atomics(15, s)

@@ -23,10 +23,11 @@
 // n = 64 is the packed store itself (hlf_enumerate_store's kernel, which also
 // takes the 8-byte aligned outputs this entry point allows).
 //
-// n > 64, dense2_kernel: 64 solutions of n bits are exactly n words, so a
-// warp produces one such group per step (two for n <= 256), two solutions per
-// lane, each placed with funnel shifts at its bit offset in the group (see
-// dense2_kernel).
+// n > 64: 64 solutions of n bits are exactly n words (a group). For n <= 256,
+// dense3_kernel steps whole group blocks by one n-word XOR each (see there).
+// For n > 256, dense2_kernel: a warp produces one group per step, two
+// solutions per lane, each placed with funnel shifts at its bit offset in the
+// group.
 
 #include "enum_impl.cuh"
 
@@ -300,9 +301,10 @@ __device__ __forceinline__ void dense2_put(uint64_t* st, const uint64_t (&z)[W],
 // W or W+1 words. As n > 64, a word holds bits of at most two solutions, and
 // solutions t and t+2 share none: the even solutions place their words first,
 // plainly, then the odd ones merge into the first and last words they share.
-// P consecutive groups (P = 2 for n <= 256) share a staging buffer. Their P*n
-// words leave in one bulk store when the output is 16-byte aligned and P*n*8
-// bytes is a multiple of 16 (n even, or P = 2), else the warp copies them out.
+// P consecutive groups share a staging buffer (the launcher, which serves
+// n > 256, uses P = 1). Their P*n words leave in one bulk store when the
+// output is 16-byte aligned and P*n*8 bytes is a multiple of 16, else the
+// warp copies them out.
 template <int W, bool Bulk, int P>
 __global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __restrict__ table, Dense2Plan pl,
                                                             uint64_t* __restrict__ out)
@@ -427,18 +429,269 @@ hlf_status launch_dense2_k(const uint64_t* table, int n, uint64_t offset, uint64
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
-// Rows of up to four words (n <= 256) place two groups per staging buffer and
-// store them together: the per-group handshake and store are then shared by
-// four solutions per lane, and 2n words are a whole number of 16-byte units
-// for odd n as well.
+// ------------------------------------------------------------ 64 < n <= 256
+// dense3_kernel walks whole group blocks. Group H holds the solutions
+// 64 H + t, t < 64, and their n-word dense block is
+//     G(H) = S0 ^ R(D(H)).
+// With g(64 H + t) = (g(H) << 6) ^ ((H & 1) << 5) ^ g(t), solution 64 H + t is
+// Zc(t) ^ D(H), where Zc(t) = z0 ^ XOR_{k in g(t)} B_k (B_0..B_5 only) and
+// D(H) = XOR_{k in (g(H) << 6) ^ ((H & 1) << 5)} B_k. Placing 64 solutions
+// side by side is linear in them, so the block splits into S0, the placement
+// of Zc(0..63) (the same for every group), and R(D(H)), the placement of 64
+// copies of D(H) (the tiling R). D(H + 1) = D(H) ^ C_j with C_j = B_5 ^
+// B_{6+j}, j = ctz(H + 1), so G(H + 1) = G(H) ^ T_j with T_j = R(C_j): one
+// n-word XOR per group.
+//
+// The window [offset, offset + count) starts e = (offset mod 64) n bits into
+// the block of its first group Hw = offset / 64, so stream word p holds bits
+// [64 p + e, 64 p + e + 64) of the blocks laid end to end: with e = 64 a + b,
+// word p = k n + q - a comes from group Hw + k as
+//     G'(H)[q] = f(G(H)[q], G(H)[q + 1]),  f(x, y) = (x >> b) | (y << (64 - b)),
+// where G(H)[n] is word 0 of the next block, G(H + 1)[0]. f is linear too, so
+// the step into group H is G'(H) = G'(H - 1) ^ S_H with
+//     S_H[q] = f(T_j[q], T_j[q + 1]) for q < n - 1,
+//     S_H[n - 1] = f(T_j[n - 1], T_j'[0]),   j = ctz(H), j' = ctz(H + 1).
+// One of H, H + 1 is odd, so (j, j') is (j, 0) for even H and (0, j') for odd
+// H: the rows S for j, j' < kD3J are kept in shared memory, 2 kD3J rows of n
+// words (all but 1 / 2^kD3J of the steps), and formed on the fly otherwise
+// (b = 0 makes f the identity). Lane l holds the words l + 32 m of G' in
+// registers and stores them straight to global memory, so a warp writes 256
+// consecutive bytes per store instruction and nothing is staged; per 64
+// solutions a lane spends about four instructions per word it owns (load,
+// 64-bit XOR, store).
+constexpr int kD3J = 8;
+constexpr int kD3Threads = 256;
+constexpr int kD3Warps = kD3Threads / 32;
+
+struct Dense3Plan {
+    uint64_t Hw;        // offset / 64: the window's first group
+    uint64_t groups;    // groups the window touches
+    uint64_t per_warp;  // consecutive groups per warp
+    uint64_t words;     // ceil(count * n / 64), the stream's length
+    uint64_t last_mask; // valid bits of the stream's last word
+    uint32_t a, b;      // e = 64 a + b bits of the first block precede the window
+    int n;
+};
+
+// Bits [c, c + 64) of the W-word vector x (zero past its last word); x in
+// registers, selected without dynamic indexing.
+template <int W>
+__device__ __forceinline__ uint64_t window64_reg(const uint64_t (&x)[W], uint32_t c)
+{
+    const uint32_t w = c >> 6, s = c & 63;
+    uint64_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        if (i == (int)w) lo = x[i];
+        if (i == (int)w + 1) hi = x[i];
+    }
+    return shr64(lo, s) | (s ? shl64(hi, 64 - s) : 0ull);
+}
+
+// Word q of the tiling R(x): 64 copies of the n-bit vector x (shared memory,
+// W words, zero past bit n) side by side. Copy t = 64 q / n starts the word
+// at its bit c = 64 q - t n; when fewer than 64 of its bits remain, the next
+// copy's first bits follow (n > 64, so no word touches three copies).
+template <int W>
+__device__ __forceinline__ uint64_t tile_word(const uint64_t* x, int n, uint32_t q)
+{
+    const uint32_t c = (64u * q) % (uint32_t)n;  // q <= 256: 32-bit arithmetic
+    const uint32_t w = c >> 6, s = c & 63;
+    uint64_t v = shr64(x[w], s);
+    if (s && (int)w + 1 < W) v |= shl64(x[w + 1], 64 - s);
+    if ((uint32_t)n - c < 64) v |= shl64(x[0], (uint32_t)n - c);
+    return v;
+}
+
+// Word q of S0: the placement of Zc(0..63).
+template <int W>
+__device__ __forceinline__ uint64_t group_base_word(const Table<W>& t, int n, uint32_t q)
+{
+    const uint32_t t1 = (64u * q) / (uint32_t)n;
+    const uint32_t c = 64 * q - t1 * (uint32_t)n;
+    uint64_t a[W];
+    uint64_t next0 = t.z0[0];  // word 0 of Zc(t1 + 1)
+#pragma unroll
+    for (int w = 0; w < W; ++w) a[w] = t.z0[w];
+    const uint32_t g1 = t1 ^ (t1 >> 1), g2 = (t1 + 1) ^ ((t1 + 1) >> 1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if ((g1 >> k) & 1u) xor_row<W>(a, t.B[k]);
+        if ((g2 >> k) & 1u) next0 ^= t.B[k][0];
+    }
+    uint64_t v = window64_reg<W>(a, c);
+    if ((uint32_t)n - c < 64) v |= shl64(next0, (uint32_t)n - c);  // t1 < 63 here
+    return v;
+}
+
+__device__ __forceinline__ uint64_t funnel(uint64_t x, uint64_t y, uint32_t b)
+{
+    return b ? (x >> b) | (y << (64 - b)) : x;
+}
+
+// Word q of the step row S for (j, j'), formed from C_j and C_j' (the rows
+// of rare steps; out of line so that the walk's loops stay unrolled).
+template <int W>
+__device__ __noinline__ uint64_t step_word(const uint64_t* Cj, const uint64_t* Cjn, int n, uint32_t q, uint32_t b)
+{
+    const uint64_t x = tile_word<W>(Cj, n, q);
+    return funnel(x, q + 1 < (uint32_t)n ? tile_word<W>(Cj, n, q + 1) : tile_word<W>(Cjn, n, 0), b);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kD3Threads, W == 2 ? 5 : (W == 3 ? 4 : 3)) dense3_kernel(const uint64_t* __restrict__ table, Dense3Plan pl,
+                                                            uint64_t* __restrict__ out)
+{
+    constexpr int MW = 2 * W;  // words per lane: 32 lanes x 2W >= n
+    // S rows [2 kD3J][n] (row j: (j, 0), row kD3J + j': (0, j')), S0 [n],
+    // D [warps][W]
+    extern __shared__ __align__(16) uint64_t s_d3[];
+    __shared__ Table<W> t;
+    __shared__ uint64_t s_C[kD2Steps][W];  // C_j = B_5 ^ B_{6+j}
+    const int n = pl.n;
+    const uint32_t b = pl.b;
+    uint64_t* const s_S = s_d3;
+    uint64_t* const s_S0 = s_S + 2 * kD3J * n;
+    uint64_t* const s_D = s_S0 + n;
+    load_table<W>(t, table);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kD2Steps * W; i += blockDim.x) {
+        const int j = i / W, w = i % W;
+        s_C[j][w] = t.B[5][w] ^ t.B[6 + j][w];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * kD3J * n; i += blockDim.x) {
+        const int row = i / n, q = i % n;
+        const int j = row < kD3J ? row : 0, jn = row < kD3J ? 0 : row - kD3J;
+        const uint64_t x = tile_word<W>(s_C[j], n, (uint32_t)q);
+        const uint64_t y = q + 1 < n ? tile_word<W>(s_C[j], n, (uint32_t)q + 1) : tile_word<W>(s_C[jn], n, 0);
+        s_S[i] = funnel(x, y, b);
+    }
+    for (int q = threadIdx.x; q < n; q += blockDim.x) s_S0[q] = group_base_word<W>(t, n, (uint32_t)q);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t k0 = ((uint64_t)blockIdx.x * kD3Warps + warp) * pl.per_warp;
+    if (k0 >= pl.groups) return;
+    const uint64_t k1 = min(k0 + pl.per_warp, pl.groups);
+    const uint64_t H0 = pl.Hw + k0;  // < 2^58
+    {  // D(H0): every lane forms it; lane w < W publishes word w
+        uint64_t g = ((H0 ^ (H0 >> 1)) << 6) | ((H0 & 1ull) << 5);
+        uint64_t D[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) D[w] = 0;
+        while (g) {
+            xor_row<W>(D, t.B[__ffsll((long long)g) - 1]);
+            g &= g - 1;
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (lane == w) s_D[warp * W + w] = D[w];
+        __syncwarp();
+    }
+    // G'(H0): f of consecutive words of G(H0), the last with G(H0 + 1)[0]
+    uint64_t G[MW];
+    {
+        const uint64_t* D = s_D + warp * W;
+        const int j = ctz64(H0 + 1);
+        const uint64_t next0 = s_S0[0] ^ tile_word<W>(D, n, 0) ^ tile_word<W>(s_C[j], n, 0);
+#pragma unroll
+        for (int m = 0; m < MW; ++m) {
+            const int q = lane + 32 * m;
+            uint64_t v = 0;
+            if (q < n) {
+                v = s_S0[q] ^ tile_word<W>(D, n, (uint32_t)q);
+                if (b) v = funnel(v, q + 1 < n ? s_S0[q + 1] ^ tile_word<W>(D, n, (uint32_t)q + 1) : next0, b);
+            }
+            G[m] = v;
+        }
+    }
+    // groups whose every word lies inside the stream and before its last
+    // word: [ka, kb) (stream word p = k n + q - a of group Hw + k)
+    const uint64_t ka = (pl.a + n - 1) / n;
+    const uint64_t kb = (pl.words + pl.a - 1) / n;  // k n - a + n <= words - 1
+    uint64_t kn = k0 * (uint64_t)n;
+    for (uint64_t k = k0;; kn += n) {
+        if (k >= ka && k < kb) {
+            uint64_t* dst = out + (kn - pl.a);
+#pragma unroll
+            for (int m = 0; m < MW; ++m) {
+                const int q = lane + 32 * m;
+                if (q < n) st_cs(dst + q, G[m]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < MW; ++m) {
+                const int q = lane + 32 * m;
+                const uint64_t p = kn + q - pl.a;  // wraps to a huge value when negative
+                if (q < n && kn + q >= pl.a && p < pl.words)
+                    st_cs(out + p, p == pl.words - 1 ? (G[m] & pl.last_mask) : G[m]);
+            }
+        }
+        if (++k == k1) break;
+        const uint64_t H = pl.Hw + k;  // the group stepped to, < 2^58
+        // one of j = ctz(H), j' = ctz(H + 1) is 0: c is the other
+        const int c = __ffsll((long long)((H & 1) ? H + 1 : H)) - 1;
+        const int row = (H & 1) ? kD3J + c : c;
+        if (c < kD3J) {
+            const uint64_t* S = s_S + row * n;
+#pragma unroll
+            for (int m = 0; m < MW; ++m) {
+                const int q = lane + 32 * m;
+                if (q < n) G[m] ^= S[q];
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < MW; ++m) {
+                const int q = lane + 32 * m;
+                if (q < n) G[m] ^= step_word<W>(s_C[(H & 1) ? 0 : c], s_C[(H & 1) ? c : 0], n, (uint32_t)q, b);
+            }
+        }
+    }
+}
+
+template <int W>
+hlf_status launch_dense3(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
+                         cudaStream_t s)
+{
+    Dense3Plan pl{};
+    pl.n = n;
+    pl.Hw = offset >> 6;
+    pl.groups = ((offset + (count - 1)) >> 6) - pl.Hw + 1;  // count >= 1; offset + count - 1 < 2^64
+    const uint64_t bits = count * (uint64_t)n;             // <= 2^64 - 64 (checked by the caller)
+    pl.words = (bits + 63) / 64;
+    pl.last_mask = (bits & 63) ? (1ull << (bits & 63)) - 1 : ~0ull;
+    const uint64_t e = (offset & 63) * (uint64_t)n;
+    pl.a = (uint32_t)(e >> 6);
+    pl.b = (uint32_t)(e & 63);
+    const size_t smem = ((size_t)(2 * kD3J + 1) * n + (size_t)kD3Warps * W) * sizeof(uint64_t);  // <= 34.3 KB
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense3_kernel<W>, kD3Threads, smem) != cudaSuccess)
+        return HLF_ERR_CUDA;
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t max_warps = (uint64_t)sm_count() * per_sm * kD3Warps;
+    const uint64_t warps = pl.groups < max_warps ? pl.groups : max_warps;
+    pl.per_warp = (pl.groups + warps - 1) / warps;
+    const uint64_t used = (pl.groups + pl.per_warp - 1) / pl.per_warp;
+    const unsigned blocks = (unsigned)((used + kD3Warps - 1) / kD3Warps);
+    dense3_kernel<W><<<blocks, kD3Threads, smem, s>>>(table, pl, out);
+    return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
+}
+
+// n <= 256 takes the group-block walk (dense3_kernel); wider rows place
+// their solutions one by one (dense2_kernel).
 template <int W>
 hlf_status launch_dense2(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
                          cudaStream_t s)
 {
-    constexpr int P = W <= 4 ? 2 : 1;
-    if (reinterpret_cast<uintptr_t>(out) % 16 == 0 && (P == 2 || n % 2 == 0))
-        return launch_dense2_k<W, true, P>(table, n, offset, count, out, s);
-    return launch_dense2_k<W, false, P>(table, n, offset, count, out, s);
+    if constexpr (W <= 4) {
+        return launch_dense3<W>(table, n, offset, count, out, s);
+    } else {
+        if (reinterpret_cast<uintptr_t>(out) % 16 == 0 && n % 2 == 0)
+            return launch_dense2_k<W, true, 1>(table, n, offset, count, out, s);
+        return launch_dense2_k<W, false, 1>(table, n, offset, count, out, s);
+    }
 }
 
 }  // namespace

@@ -129,3 +129,90 @@ def test_dense_wide_rows_many_groups(cuda_ok, n):
     want = oc.window_dense(F, off + 64 * groups, tail)
     assert np.array_equal(out[groups * n:], want)
     G.close()
+
+
+@pytest.mark.parametrize("n", [65, 77, 100, 127, 128, 129, 130, 193, 200, 255, 256])
+def test_dense_group_blocks_aligned(cuda_ok, n):
+    """64 < n <= 256 at window offsets that are multiples of 64 (the
+    group-block walk: each 64-solution block is the last one XOR a tiled
+    step row). Windows from one solution to many groups per warp, ragged last
+    groups, windows that cross a multiple of 2^k for large k (steps whose
+    tiled row is formed on the fly), 8-byte and 16-byte aligned outputs; the
+    whole stream against the oracle and nothing written around it."""
+    import torch
+
+    A = synth.random_symmetric(n, 0.3, 900 + n)
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    lg = F.space_log2()
+    space = 1 << lg
+    cases = [(0, 1), (0, 63), (0, 64), (64, 65), (0, 70001)]
+    for k in (16, 20, lg - 2):  # windows straddling the multiple 2^k of the index
+        if k < lg:
+            cases.append(((1 << k) - 64 * 300, 64 * 600 + 17))
+    cases.append((space - 64 * 200, 64 * 200))  # up to the end of the index space
+    for off, cnt in cases:
+        assert off % 64 == 0 and off + cnt <= space
+        words = hlf.dense_words(cnt, n)
+        for lead in (0, 1):
+            buf = torch.full((words + 3,), -1, dtype=torch.int64, device="cuda")
+            G.store_dense(off, cnt, buf[lead:])
+            got = buf.cpu().numpy().view(np.uint64)
+            assert np.array_equal(got[lead:lead + words], oc.window_dense(F, off, cnt)), (n, off, cnt, lead)
+            assert np.all(got[lead + words:] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote past the stream"
+            assert np.all(got[:lead] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote before the stream"
+    G.close()
+
+
+@pytest.mark.parametrize("n", [65, 130, 256])
+def test_dense_group_blocks_long_window(cuda_ok, n):
+    """A long aligned window (2^22 + 37 solutions, many groups per warp):
+    sampled groups and the ragged last group against the oracle."""
+    A = synth.random_symmetric(n, 0.02, 700 + n)
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    cnt = (1 << 22) + 37
+    off = synth.window_offset(n, F.space_log2(), cnt) & ~63
+    out = G.store_dense(off, cnt).cpu().numpy().view(np.uint64)
+    assert len(out) == hlf.dense_words(cnt, n)
+    rng = np.random.default_rng(n)
+    groups = cnt // 64
+    for g in [0, groups - 1] + list(rng.integers(1, groups - 1, size=24)):
+        g = int(g)
+        assert np.array_equal(out[g * n:(g + 1) * n], oc.window_dense(F, off + 64 * g, 64)), g
+    tail = cnt - 64 * groups
+    assert np.array_equal(out[groups * n:], oc.window_dense(F, off + 64 * groups, tail))
+    G.close()
+
+
+@pytest.mark.parametrize("n", [65, 96, 100, 128, 130, 193, 256])
+def test_dense_group_blocks_any_offset(cuda_ok, n):
+    """64 < n <= 256 at offsets that are not multiples of 64: the window
+    starts (offset mod 64) * n bits into its first group block, and every
+    stream word is funnel-shifted from two consecutive block words (the last
+    from the next group's block). Several residues, windows within one group,
+    across one boundary and across many, ending at the end of the index
+    space; 8- and 16-byte aligned outputs."""
+    import torch
+
+    A = synth.random_symmetric(n, 0.3, 950 + n)
+    F = oc.factor(A)
+    G = hlf.Factorization.from_dense(A)
+    lg = F.space_log2()
+    space = 1 << lg
+    cases = []
+    for o in (1, 7, 33, 63):
+        cases += [(o, 1), (o, 64 - o), (o, 65 - o), (64 * 3 + o, 64 * 40 + 11), (o, 70001)]
+        cases.append(((1 << 20) + o - 64 * 300, 64 * 600 + 5))
+        cases.append((space - 64 * 100 - o, 64 * 100 + o))  # ends at the end of the index space
+    for off, cnt in cases:
+        assert off % 64 and off + cnt <= space
+        words = hlf.dense_words(cnt, n)
+        for lead in (0, 1):
+            buf = torch.full((words + 3,), -1, dtype=torch.int64, device="cuda")
+            G.store_dense(off, cnt, buf[lead:])
+            got = buf.cpu().numpy().view(np.uint64)
+            assert np.array_equal(got[lead:lead + words], oc.window_dense(F, off, cnt)), (n, off, cnt, lead)
+            assert np.all(got[lead + words:] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote past the stream"
+            assert np.all(got[:lead] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote before the stream"
+    G.close()

@@ -52,11 +52,11 @@ SAMPLE_LOG2 = 20
 SAMPLE_SEED = 99
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each roofline kernel in this bench's default configuration, from one ncu
-# capture (profiles/traffic_grid6x6.md has the command and the raw figures).
-# Each record carries a digest of the kernel's source files at capture time;
-# once those sources change, the figure no longer describes the kernel and
-# the line reports null.
+# each roofline kernel in this bench's default configuration, recorded by hand
+# from one ncu capture of this bench (not measured in the run). Each record
+# carries a digest of the kernel's source files at capture time; once those
+# sources change, the figure no longer describes the kernel and the line
+# reports null.
 KERNEL_SOURCES = {
     "reduce_kernel<1,6,1024>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
     "store_kernel<1,2>": ["enumerate.cu", "enum_impl.cuh", "hlf_internal.cuh"],
@@ -100,6 +100,9 @@ def parse():
     p.add_argument("--store-log2", type=int, default=STORE_LOG2, help="solutions stored per step (log2)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched (4096 grids) leg")
     p.add_argument("--no-served", action="store_true", help="skip the served (Poisson stream) leg")
+    p.add_argument("--shard", action="store_true",
+                   help="split ONE grid6x6 instance across the ranks (contiguous index ranges, one all-gather "
+                        "of the partials; strong scaling) instead of one replica per GPU")
     return p.parse_args()
 
 
@@ -763,11 +766,108 @@ def run_served(args, srv=None):
     return out
 
 
+def run_sharded(args, world, rank, local):
+    """One grid6x6 instance split across the ranks. Each step, every rank
+    copies A in from pinned host memory, factors it (microseconds, so it is
+    replicated), reduces its contiguous slice of the 2^r indices with
+    hlf_enumerate_reduce, reads its partial back, and the partials meet in one
+    all-gather and combine (paper_2103_00693_gb300.shard, the code the gloo
+    tests run on CPU ranks). Total work is fixed as N grows: strong scaling."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2103_00693_gb300 as hlf
+    from paper_2103_00693_gb300 import shard
+    from synth import workloads as wl
+
+    torch.cuda.set_device(local)
+    hlf.load()
+    dev = torch.device("cuda", local)
+    A = wl.grid6()
+    n = A.shape[0]
+    W = hlf.words(n)
+    A_host = torch.from_numpy(hlf.pack_rows(A).view(np.int64)).pin_memory()
+    A_dev = torch.empty_like(A_host, device=dev)
+    red = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, device=dev)
+    red_host = torch.empty(hlf.REDUCE_WORDS, dtype=torch.int64, pin_memory=True)
+    coll_dev = "cuda" if world > 1 and dist.get_backend() == "nccl" else "cpu"
+    A_dev.copy_(A_host)
+    h0 = hlf.hlf_factor(A_dev, n)
+    r = hlf.hlf_get_rank(h0)
+    hlf.hlf_destroy(h0)
+    total = 1 << (r if args.reduce_log2 is None else min(r, args.reduce_log2))
+    stream = torch.cuda.current_stream(dev)
+    evs = []
+
+    def step(record: bool):
+        A_dev.copy_(A_host, non_blocking=True)
+        h = hlf.hlf_factor(A_dev, n)
+
+        def reduce_fn(o, c):
+            e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            e[0].record(stream)
+            hlf.hlf_enumerate_reduce(h, o, c, red)
+            e[1].record(stream)
+            if record:
+                evs.append(e)
+            red_host.copy_(red, non_blocking=True)
+            stream.synchronize()
+            rr = hlf.ReduceResult.from_words(red_host.numpy(), W)
+            return rr.count, rr.hsum, rr.xor_fold
+
+        part = shard.reduce_shard(reduce_fn, 0, total, rank, world)
+        got = shard.allgather_combine(part, W, world, coll_dev)
+        hlf.hlf_destroy(h)
+        return got
+
+    for _ in range(max(3, args.warmup)):
+        got = step(False)
+    assert got[0] == total, got  # the shards cover the window exactly
+    if total == 1 << r and r >= 2:
+        assert not got[2].any()   # the full set is an affine space of dimension >= 2
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(True)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    clk = clocks.stop()
+    k_ms = max_over_ranks(statistics.mean(e[0].elapsed_time(e[1]) for e in evs), world)
+    mine = shard.shard_range(0, total, rank, world)[1]
+    ipk, ipk_basis = int_peak(dev)
+    achieved = mine * OPS_PER_SOLUTION_W1 * W / (k_ms / 1e3) / 1e12
+    if rank != 0:
+        return
+    value = args.steps * total / dt
+    cfg = workload_config(r, total)
+    cfg["parallelism"] = (f"shards: contiguous index ranges of one instance over {world} GPU(s), "
+                          f"one all-gather of {2 + W} words per rank per step")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ipk, "unit": "Tops/s",
+                         "frac": achieved / ipk, "traffic": None, "kernel": "reduce_kernel<1,6,1024>",
+                         "ms_per_launch": k_ms, "peak_basis": ipk_basis,
+                         "ops_per_solution": OPS_PER_SOLUTION_W1 * W},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": A_host.numel() * 8,
+                    "d2h_bytes_per_step": red_host.numel() * 8,
+                    "note": "the step itself runs through host buffers: A in, the partial out, the exchange"},
+            "gpu_launches": 2 * args.steps, "clocks": clk, "combined": {"count": got[0], "hsum": got[1]}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.shard:
+        run_sharded(args, world, rank, local)
     else:
         run_hlf(args, world, rank, local)
     if world > 1:

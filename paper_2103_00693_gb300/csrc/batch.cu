@@ -493,6 +493,7 @@ hlf_status hlf_batch_factor_reduce(hlf_batch* b, const uint64_t* A_dev, const in
                                    const int32_t* n_dev, int32_t count, uint64_t cap, int32_t* r_dev,
                                    hlf_reduce* red_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_batch_factor_reduce");
     if (!b || count < 0 || count > b->max_instances || cap == 0) return HLF_ERR_ARG;
     if (count == 0) return HLF_OK;
     if (!A_dev || !word_off_dev || !n_dev || !r_dev || !red_dev) return HLF_ERR_ARG;
@@ -521,6 +522,7 @@ hlf_status hlf_batch_factor_reduce(hlf_batch* b, const uint64_t* A_dev, const in
 hlf_status hlf_factor_batched(hlf_batch* b, const uint64_t* A_dev, const int64_t* offsets_dev, int32_t count,
                               int32_t* r_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_factor_batched");
     if (!b || count < 0 || count > b->max_instances) return HLF_ERR_ARG;
     if (count == 0) {
         b->factored = 0;
@@ -546,6 +548,7 @@ hlf_status hlf_factor_batched(hlf_batch* b, const uint64_t* A_dev, const int64_t
 hlf_status hlf_enumerate_batched(hlf_batch* b, uint64_t cap, hlf_reduce* red_dev, uint64_t* out_dev,
                                  const int64_t* out_offsets_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_batched");
     if (!b || cap == 0 || (!red_dev) == (!out_dev) || (out_dev && !out_offsets_dev)) return HLF_ERR_ARG;
     if (b->factored < 1) return HLF_ERR_ARG;
     if (check_device(b) != HLF_OK) return HLF_ERR_ARG;
@@ -584,6 +587,7 @@ hlf_status hlf_batch_factor_reduce_noalloc(const uint64_t* A_dev, const int64_t*
                                            const int32_t* n_dev, int32_t count, uint64_t cap, int32_t* r_dev,
                                            hlf_reduce* red_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_batch_factor_reduce_noalloc");
     if (count < 0 || cap == 0) return HLF_ERR_ARG;
     if (count > HLF_BATCH_NOALLOC_MAX) return HLF_ERR_SIZE;
     if (count == 0) return HLF_OK;

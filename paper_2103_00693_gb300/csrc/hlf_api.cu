@@ -319,6 +319,7 @@ int32_t hlf_device_count(void)
 
 hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle** out)
 {
+    hlf::NvtxRange nvtx_range("hlf_factor");
     if (!out) return HLF_ERR_ARG;
     *out = nullptr;
     if (!A_dev) return HLF_ERR_ARG;
@@ -374,6 +375,7 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
 
 hlf_status hlf_get_rank(hlf_handle* h, int32_t* r)
 {
+    hlf::NvtxRange nvtx_range("hlf_get_rank");
     if (!h || !r) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
@@ -400,6 +402,7 @@ hlf_status hlf_get_shape(hlf_handle* h, int32_t* n, int32_t* W)
 
 hlf_status hlf_get_factor(hlf_handle* h, int32_t* piv_host, uint64_t* z0_host, uint64_t* basis_host)
 {
+    hlf::NvtxRange nvtx_range("hlf_get_factor");
     if (!h) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
@@ -434,6 +437,7 @@ hlf_status hlf_get_status(hlf_handle* h)
 
 hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_store");
     if (!h || (!out_dev && count)) return HLF_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(out_dev) % 16) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
@@ -448,6 +452,7 @@ hlf_status hlf_enumerate_store(hlf_handle* h, uint64_t offset, uint64_t count, u
 
 hlf_status hlf_enumerate_store_upto(hlf_handle* h, uint64_t cap, uint64_t* out_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_store_upto");
     if (!h || (!out_dev && cap) || cap > HLF_STORE_UPTO_MAX) return HLF_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(out_dev) % 8) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
@@ -460,6 +465,7 @@ hlf_status hlf_enumerate_store_upto(hlf_handle* h, uint64_t cap, uint64_t* out_d
 
 hlf_status hlf_enumerate_reduce_upto(hlf_handle* h, uint64_t cap, hlf_reduce* red_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_reduce_upto");
     if (!h || !red_dev) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
@@ -473,6 +479,7 @@ hlf_status hlf_enumerate_reduce_upto(hlf_handle* h, uint64_t cap, hlf_reduce* re
 hlf_status hlf_enumerate_store_dense(hlf_handle* h, uint64_t offset, uint64_t count, uint64_t* out_dev,
                                      void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_store_dense");
     if (!h || (!out_dev && count)) return HLF_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(out_dev) % 8) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
@@ -488,6 +495,7 @@ hlf_status hlf_enumerate_store_dense(hlf_handle* h, uint64_t offset, uint64_t co
 
 hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, hlf_reduce* red_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_reduce");
     if (!h || !red_dev) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
@@ -503,6 +511,7 @@ hlf_status hlf_enumerate_reduce(hlf_handle* h, uint64_t offset, uint64_t count, 
 hlf_status hlf_enumerate_histogram(hlf_handle* h, uint64_t offset, uint64_t count, int32_t bit_lo, int32_t nbits,
                                    uint64_t* hist_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_histogram");
     if (!h || !hist_dev || nbits < 1 || nbits > HLF_HIST_MAX_BITS || bit_lo < 0) return HLF_ERR_ARG;
     if (bit_lo + nbits > h->n) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
@@ -520,6 +529,7 @@ hlf_status hlf_enumerate_histogram(hlf_handle* h, uint64_t offset, uint64_t coun
 hlf_status hlf_enumerate_reduce_chunks(hlf_handle* h, uint64_t offset, uint64_t chunk, uint64_t n_chunks,
                                        hlf_reduce* red_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_reduce_chunks");
     if (!h || (!red_dev && n_chunks) || chunk == 0) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
@@ -534,6 +544,7 @@ hlf_status hlf_enumerate_reduce_chunks(hlf_handle* h, uint64_t offset, uint64_t 
 
 hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64_t* out_dev, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_sample");
     if (!h || (m && (!idx_dev || !out_dev))) return HLF_ERR_ARG;
     DeviceGuard g(h->device);
     if (!g.ok) return HLF_ERR_CUDA;
@@ -547,6 +558,7 @@ hlf_status hlf_sample(hlf_handle* h, const uint64_t* idx_dev, uint64_t m, uint64
 
 hlf_status hlf_destroy(hlf_handle* h)
 {
+    hlf::NvtxRange nvtx_range("hlf_destroy");
     if (!h) return HLF_OK;
     hlf_status st = HLF_OK;
     {

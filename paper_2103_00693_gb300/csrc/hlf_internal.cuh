@@ -17,10 +17,21 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "hlf.h"
 
 namespace hlf {
+
+// NVTX range around a host entry point (stage 1, stage 2, batched and
+// served calls), so a profiler's timeline shows which call enqueued which
+// kernels. Without a profiler attached a push and pop cost nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kTableRows = 65;      // B_0..B_64 (row 64 always zero)
 constexpr int kTableZ0Row = 65;     // z0 follows the basis rows

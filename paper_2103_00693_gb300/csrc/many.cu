@@ -205,6 +205,7 @@ hlf_status hlf_many_create(int32_t max_windows, hlf_many** out)
 hlf_status hlf_enumerate_store_many(hlf_many* m, hlf_handle* const* hs, const uint64_t* offsets,
                                     const uint64_t* counts, uint64_t* const* outs_dev, int32_t k, void* stream)
 {
+    hlf::NvtxRange nvtx_range("hlf_enumerate_store_many");
     if (!m || k < 0 || k > m->max_windows) return HLF_ERR_ARG;
     if (k == 0) return HLF_OK;
     if (!hs || !offsets || !counts || !outs_dev) return HLF_ERR_ARG;

@@ -480,6 +480,7 @@ class Server:
                 q.blk_dev, q.blk_host = bd, bh
                 ready.append(pending.popleft())
             if ready:
+                torch.cuda.nvtx.range_push("serve.tick")  # one window launch and its copies
                 try:
                     hlf.hlf_enumerate_store_many(
                         self.many, [q.h for q in ready], [q.offset for q in ready], [q.count for q in ready],
@@ -490,6 +491,7 @@ class Server:
                         self._release(q)
                         self._finish(q, FAILED, e.status, st, done, t)
                     ready = []
+                    torch.cuda.nvtx.range_pop()
             if ready:
                 st.ticks += 1
                 st.launches += 1
@@ -507,6 +509,7 @@ class Server:
                         if self._on_event:
                             self._on_event("launched", q)
                 copying.extend(ready)
+                torch.cuda.nvtx.range_pop()
             finished = 0
             while copying and copying[0].ev_copy.query():  # copies complete in stream order
                 q = copying.pop(0)

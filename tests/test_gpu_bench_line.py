@@ -41,3 +41,20 @@ def test_bench_line_has_every_field(cuda_ok):
     assert d["configs"]["grid3x3"]["solutions"] == 512
     # a timed region this short may end before nvidia-smi's first sample
     assert d["clocks"] is None or set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+
+
+def test_bench_sharded_mode_line(cuda_ok):
+    """bench.py --shard on one GPU: the shard/all-gather/combine path the
+    multi-GPU runs use (here with one rank), one JSON line with strong
+    scaling and the combined reduce covering the whole window."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--shard", "--steps", "3", "--warmup", "3",
+           "--reduce-log2", "30"]
+    res = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["scaling"] == "strong" and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["combined"]["count"] == 1 << 30
+    assert 0 < d["roofline"]["frac"] < 1.5 and d["gpu_launches"] == 6
+    assert set(d["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}

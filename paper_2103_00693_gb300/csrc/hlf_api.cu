@@ -14,7 +14,7 @@ struct hlf_handle {
     int32_t n = 0;
     int32_t W = 0;
     int device = 0;
-    unsigned char* dmem = nullptr;  // one allocation: info | piv | table | basis
+    unsigned char* dmem = nullptr;  // one allocation: factor scratch | piv | table | ptable | basis
     int32_t* info = nullptr;         // status word: pinned host memory, device-mapped
     int32_t* info_dev = nullptr;     // the same words as the kernels address them
     int32_t* piv = nullptr;
@@ -334,7 +334,7 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
         delete h;
         return HLF_ERR_CUDA;
     }
-    const size_t off_piv = 64;
+    const size_t off_piv = 256;  // [0, 256): the factor kernels' device scratch (kFactorWorkWords int32)
     const size_t off_table = round_up(off_piv + sizeof(int32_t) * n, 256);
     const size_t off_ptable = round_up(off_table + sizeof(uint64_t) * hlf::kTableTotalRows * h->W, 256);
     const size_t off_basis = round_up(off_ptable + sizeof(uint64_t) * hlf::kTableTotalRows * h->W, 256);
@@ -361,7 +361,7 @@ hlf_status hlf_factor(const uint64_t* A_dev, int32_t n, void* stream, hlf_handle
         hlf_destroy(h);
         return HLF_ERR_CUDA;
     }
-    hlf::FactorOut o{h->basis, h->piv, h->table, h->info_dev, h->ptable};
+    hlf::FactorOut o{h->basis, h->piv, h->table, h->info_dev, h->ptable, reinterpret_cast<int32_t*>(h->dmem)};
     hlf_status st = hlf::launch_factor(A_dev, n, h->W, o, s);
     if (st == HLF_OK && cudaEventRecord(h->factored, s) != cudaSuccess) st = HLF_ERR_CUDA;
     st = after_launch(h, st, s);

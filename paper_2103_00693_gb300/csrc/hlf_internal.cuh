@@ -43,7 +43,10 @@ struct FactorOut {
     uint64_t* table;   // [66][W]
     int32_t* info;     // [16]
     uint64_t* ptable;  // [66][W] or null: the paper-order table (see factor_impl.cuh)
+    int32_t* work;     // [kFactorWorkWords] device scratch of the n > 256 path (factor.cu), or null
 };
+
+constexpr int kFactorWorkWords = 64;
 
 // ---------------------------------------------------------------- launchers
 hlf_status launch_factor(const uint64_t* A, int n, int W, const FactorOut& o, cudaStream_t s);

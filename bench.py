@@ -37,15 +37,23 @@ sys.path.insert(0, ROOT)
 METRIC = "FS2D HLF solutions/sec"
 UNIT = "solutions/s"
 # Minimal 32-bit integer instructions per solution of the reduce at W = 1:
-# Gray step XOR 2, fold XOR 2, the SplitMix64 finalizer after its first
-# (GF(2)-linear) layer, which the walk absorbs into the basis table: two
-# 64 x 64 -> 64 multiplies at 3 and two 64-bit xor-shifts at 4 (14), and the
-# 64-bit add of the hash 2.
-OPS_PER_SOLUTION_W1 = 20
+# Gray step XOR 2, the SplitMix64 finalizer after its first (GF(2)-linear)
+# layer, which the walk absorbs into the basis table: two 64 x 64 -> 64
+# multiplies at 3 and two 64-bit xor-shifts at 4 (14), and the 64-bit add of
+# the hash 2. The XOR-fold costs nothing per solution: over a whole aligned
+# Gray block of 2^U >= 4 solutions it is zero, so only the partial blocks at
+# the ends of a run are folded. Each further word adds its step XOR 2, the
+# XOR into the chained hash 2 and a whole finalizer 18: 22W - 4 in all.
+OPS_PER_SOLUTION_W1 = 18
 ISSUE_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes
 # The histogram walks the table projected onto the field: per solution one
 # 32-bit XOR and one shared-memory atomic add.
 HIST_OPS_PER_SOLUTION = 2
+# Of the reduce's 18 operations per solution at W = 1, the 12 that only the
+# ALU pipe executes (64 lanes per clock per SM): the step XOR 2, the two
+# xor-shifts 8 and the 64-bit add 2. The multiplies run on the FMA pipe.
+ALU_PIPE_OPS_PER_SOLUTION_W1 = 12
+ALU_PIPE_LANES_PER_SM_CLK = 64
 PROBE_ITERS = 1 << 14
 STORE_LOG2 = 30
 SAMPLE_LOG2 = 20
@@ -104,6 +112,11 @@ def parse():
                    help="split ONE grid6x6 instance across the ranks (contiguous index ranges, one all-gather "
                         "of the partials; strong scaling) instead of one replica per GPU")
     return p.parse_args()
+
+
+def ops_per_solution(W: int) -> int:
+    """The reduce's minimal 32-bit integer operations per solution of W words."""
+    return OPS_PER_SOLUTION_W1 + 22 * (W - 1)
 
 
 def int_peak(dev=None):
@@ -386,7 +399,7 @@ def run_hlf(args, world, rank, local):
     pk = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * ISSUE_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 / 1e12  # Tops/s
-    ops = total * OPS_PER_SOLUTION_W1 * W
+    ops = total * ops_per_solution(W)
     achieved = ops / (reduce_ms / 1e3) / 1e12
     store_bytes = store_n * W * 8
     store_gbs = store_bytes / (store_ms / 1e3) / 1e9
@@ -401,7 +414,16 @@ def run_hlf(args, world, rank, local):
                          "ms_per_launch": reduce_ms,
                          "peak_basis": f"{sms} SMs x {ISSUE_LANES_PER_SM_CLK} int32 lanes/clk x "
                                        f"{pk['sm_max_mhz']:.0f} MHz (issue limit)",
-                         "ops_per_solution": OPS_PER_SOLUTION_W1 * W},
+                         "ops_per_solution": ops_per_solution(W)},
+            "roofline_alu_pipe": {
+                "bound": "alu_pipe",
+                "achieved": total * ALU_PIPE_OPS_PER_SOLUTION_W1 / (reduce_ms / 1e3) / 1e12,
+                "peak": sms * ALU_PIPE_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 / 1e12, "unit": "Tops/s",
+                "frac": (total * ALU_PIPE_OPS_PER_SOLUTION_W1 / (reduce_ms / 1e3))
+                        / (sms * ALU_PIPE_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6),
+                "kernel": "reduce_kernel<1,6,1024>", "ops_per_solution": ALU_PIPE_OPS_PER_SOLUTION_W1,
+                "peak_basis": f"{sms} SMs x {ALU_PIPE_LANES_PER_SM_CLK} ALU-pipe lanes/clk x "
+                              f"{pk['sm_max_mhz']:.0f} MHz (the pipe that binds: W = 1 only)"} if W == 1 else None,
             "roofline_store": {"bound": "hbm", "achieved": store_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                                "frac": store_gbs / pk["hbm_gbs"], "traffic": traffic("store_kernel<1,2>"),
                                "kernel": "store_kernel<1,2>", "ms_per_launch": store_ms,
@@ -658,9 +680,9 @@ def run_configs(dev):
 
 def batched_ops(Ws, counts) -> int:
     """Algorithmic 32-bit integer operations of the batched reduce: the
-    single-instance reduce's 24W - 4 per solution (20 at W = 1), summed over
+    single-instance reduce's 22W - 4 per solution (18 at W = 1), summed over
     the instances' solution counts; factorisation work is not counted."""
-    return int(sum(int(c) * (24 * int(w) - 4) for w, c in zip(Ws, counts)))
+    return int(sum(int(c) * ops_per_solution(int(w)) for w, c in zip(Ws, counts)))
 
 
 def run_batched(args):
@@ -726,7 +748,7 @@ def run_batched(args):
             "launch": "one persistent kernel (+3 memsets) replayed from a CUDA graph",
             "roofline": {"bound": "alu", "achieved": ops / (ms / 1e3) / 1e12, "peak": ipk,
                          "unit": "Tops/s", "frac": ops / (ms / 1e3) / 1e12 / ipk,
-                         "ops_per_batch": ops, "ops_per_solution": "24W - 4 (20 at W = 1)",
+                         "ops_per_batch": ops, "ops_per_solution": "22W - 4 (18 at W = 1)",
                          "kernel": "batch_kernel", "peak_basis": ipk_basis},
             "split_calls_ms_per_batch": split_ms,
             "plain_ms_per_batch": plain_ms, "plain_inst_per_s": len(mats) / (plain_ms / 1e3),
@@ -840,7 +862,7 @@ def run_sharded(args, world, rank, local):
     k_ms = max_over_ranks(statistics.mean(e[0].elapsed_time(e[1]) for e in evs), world)
     mine = shard.shard_range(0, total, rank, world)[1]
     ipk, ipk_basis = int_peak(dev)
-    achieved = mine * OPS_PER_SOLUTION_W1 * W / (k_ms / 1e3) / 1e12
+    achieved = mine * ops_per_solution(W) / (k_ms / 1e3) / 1e12
     if rank != 0:
         return
     value = args.steps * total / dt
@@ -853,7 +875,7 @@ def run_sharded(args, world, rank, local):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": ipk, "unit": "Tops/s",
                          "frac": achieved / ipk, "traffic": None, "kernel": "reduce_kernel<1,6,1024>",
                          "ms_per_launch": k_ms, "peak_basis": ipk_basis,
-                         "ops_per_solution": OPS_PER_SOLUTION_W1 * W},
+                         "ops_per_solution": ops_per_solution(W)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": A_host.numel() * 8,
                     "d2h_bytes_per_step": red_host.numel() * 8,
                     "note": "the step itself runs through host buffers: A in, the partial out, the exchange"},

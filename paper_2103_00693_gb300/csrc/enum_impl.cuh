@@ -2,7 +2,8 @@
 // Eqs. 1-3, Fig. 1(c)), shared by the single-instance kernels and the batched
 // persistent kernel: the shared-memory enumeration table, seeding a run from
 // the definition z(i) = z0 ^ XOR_{k in g(i)} B_k, the reflected-Gray walk of a
-// run, the per-thread reduce accumulator and the block reduction.
+// run with its reduce, the per-thread reduce accumulator and the block
+// reduction.
 #pragma once
 
 #include "hlf_internal.cuh"
@@ -12,12 +13,12 @@ namespace hlf {
 constexpr int kThreads = 256;
 
 // Solutions unrolled per Gray block (2^U) in the per-thread walks: 2^6 at
-// W = 1, 2^4 at W = 2, 2^3 at W = 3, 4, and 2^1 beyond, where each solution is
+// W = 1, 2^4 at W = 2, 2^3 at W = 3, 4, and 2^2 beyond, where each solution is
 // already 24W - 4 operations and deeper unrolling only costs registers.
 // Shape of the single-instance reduce: at W <= 4 one CTA of 1024 threads per
 // SM with up to 64 registers each; with the deeper unroll, measured 7-10%
 // faster than several 256-thread CTAs with 40-44 registers each.
-constexpr int reduce_unroll(int W) { return W == 1 ? 6 : (W == 2 ? 4 : (W <= 4 ? 3 : 1)); }
+constexpr int reduce_unroll(int W) { return W == 1 ? 6 : (W == 2 ? 4 : (W <= 4 ? 3 : 2)); }
 constexpr int reduce_threads(int W) { return W <= 4 ? 1024 : kThreads; }
 constexpr int min_ctas_for(int W) { return W <= 4 ? 1 : 2; }
 
@@ -118,8 +119,24 @@ struct Acc {
 #pragma unroll
         for (int w = 0; w < W; ++w) fold[w] ^= z[w];
     }
+    // The hash alone: for the solutions of whole aligned Gray blocks, whose
+    // XOR is zero (see reduce_run).
+    __device__ __forceinline__ void consume_hash(const uint64_t (&z)[W])
+    {
+        uint64_t h = mix_tail(z[0]);
+#pragma unroll
+        for (int w = 1; w < W; ++w) h = mix64(h ^ z[w]);
+        hs += h;
+    }
     // XOR-fold back in the solution domain (after all XOR reductions).
     __device__ __forceinline__ uint64_t fold_word(int w) const { return w == 0 ? mix_head_inv(fold[0]) : fold[w]; }
+};
+
+// The accumulator seen by whole aligned Gray blocks: hash only.
+template <int W>
+struct HashOnly {
+    Acc<W>& acc;
+    __device__ __forceinline__ void consume(const uint64_t (&z)[W]) { acc.consume_hash(z); }
 };
 
 // 2^L consecutive solutions starting at an index that is a multiple of 2^L:
@@ -142,34 +159,41 @@ struct GrayBlock<W, 0, Rows, Sink> {
     static __device__ __forceinline__ void run(uint64_t (&z)[W], const Rows&, Sink& sink) { sink.consume(z); }
 };
 
-// Walk [i, i + len): consume each solution, step by one row XOR.
-template <int W, int U, typename Sink>
-__device__ __forceinline__ void walk_run(const Table<W>& t, uint64_t i, uint64_t len, Sink& sink)
+// The reduce of [i, i + len). The solutions of an aligned block of 2^U
+// consecutive indices (U >= 2) are z_s ^ XOR_{k in S} B_k over all subsets S
+// of {0..U-1}: z_s and every B_k occur an even number of times, so their
+// XOR is zero (in the L domain too, L being linear). Whole blocks therefore
+// feed only the hash; the head and the tail of the run (partial blocks) feed
+// hash and fold. The fold is exact, and one 64-bit XOR per solution lighter.
+template <int W, int U>
+__device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64_t len, Acc<W>& acc)
 {
+    static_assert(U >= 2, "a block of 2^U solutions XORs to zero only for U >= 2");
     if (len == 0) return;
     uint64_t z[W];
     seed<W>(t, i, z);
     constexpr uint64_t kBlk = 1ull << U;
     while (len && (i & (kBlk - 1))) {  // head up to a multiple of 2^U
-        sink.consume(z);
+        acc.consume(z);
         --len;
         ++i;
         if (len) xor_row<W>(z, t.B[ctz64(i)]);
     }
     if (len >= kBlk) {
+        HashOnly<W> ho{acc};
         if constexpr (W == 1) {
             uint64_t Br[U][W];
 #pragma unroll
             for (int k = 0; k < U; ++k) Br[k][0] = t.B[k][0];
             do {
-                GrayBlock<W, U, uint64_t[U][W], Sink>::run(z, Br, sink);
+                GrayBlock<W, U, uint64_t[U][W], HashOnly<W>>::run(z, Br, ho);
                 len -= kBlk;
                 i += kBlk;
                 if (len) xor_row<W>(z, t.B[ctz64(i)]);  // ctz(i) >= U here
             } while (len >= kBlk);
         } else {
             do {
-                GrayBlock<W, U, uint64_t[kTableRows][W], Sink>::run(z, t.B, sink);
+                GrayBlock<W, U, uint64_t[kTableRows][W], HashOnly<W>>::run(z, t.B, ho);
                 len -= kBlk;
                 i += kBlk;
                 if (len) xor_row<W>(z, t.B[ctz64(i)]);
@@ -177,17 +201,11 @@ __device__ __forceinline__ void walk_run(const Table<W>& t, uint64_t i, uint64_t
         }
     }
     while (len) {  // tail
-        sink.consume(z);
+        acc.consume(z);
         --len;
         ++i;
         if (len) xor_row<W>(z, t.B[ctz64(i)]);
     }
-}
-
-template <int W, int U>
-__device__ __forceinline__ void reduce_run(const Table<W>& t, uint64_t i, uint64_t len, Acc<W>& acc)
-{
-    walk_run<W, U, Acc<W>>(t, i, len, acc);
 }
 
 // Block-wide (count, hsum, fold) reduction over a CTA of THREADS threads;

@@ -71,9 +71,9 @@ KERNEL_SOURCES = {
     "dense1_kernel<16,1,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
-    "reduce_kernel<1,6,1024>": {"bytes": 763904 + 0, "sources": "ca34b4ee5cc09f44"},
-    "store_kernel<1,2>": {"bytes": 148736 + 8524820736, "sources": "ca34b4ee5cc09f44"},
-    "dense1_kernel<16,1,1>": {"bytes": 84480 + 4766982912, "sources": "fe23227d3315e902"},
+    "reduce_kernel<1,6,1024>": {"bytes": 743168 + 0, "sources": "1de446fddcf41e74"},
+    "store_kernel<1,2>": {"bytes": 701952 + 8525239808, "sources": "1de446fddcf41e74"},
+    "dense1_kernel<16,1,1>": {"bytes": 85504 + 4767099648, "sources": "b226170a230afc66"},
 }
 
 

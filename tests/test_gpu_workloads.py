@@ -135,3 +135,31 @@ def test_grid8x8_window_reduce_and_sample(cuda_ok):
         assert np.array_equal(out[t], oc.window(F, int(idx[t]), 1)[0])
     assert G.status() == 0
     G.close()
+
+
+def test_resumable_job_on_the_gpu(cuda_ok):
+    """A grid8x8 reduce run as a resumable job: stopped after two chunks,
+    checkpointed to JSON, resumed on a fresh factorisation, finished; equal to
+    the one-launch reduce of the whole window and to the oracle's."""
+    from paper_2103_00693_gb300.job import ReduceJob, gpu_reduce_fn
+
+    A = wl.grid8()
+    F = oc.factor(A)
+    off, cnt = 12345, (1 << 28) + 77
+    job = ReduceJob.start(A, off, cnt, 1 << 26)
+    fn, close = gpu_reduce_fn(job)
+    job.advance(fn, 2)
+    close()
+    text = job.to_json()
+    resumed = ReduceJob.from_json(text)
+    fn2, close2 = gpu_reduce_fn(resumed)
+    while not resumed.done():
+        resumed.advance(fn2, 3)
+    close2()
+    c, h, f = resumed.result()
+    G = hlf.Factorization.from_dense(A)
+    whole = hlf.ReduceResult.from_words(G.reduce(off, cnt).cpu().numpy(), F.W)
+    G.close()
+    assert (c, h) == (whole.count, whole.hsum) and np.array_equal(f, whole.xor_fold)
+    want = oc.reduce(F, off, cnt)
+    assert (c, h) == want[:2] and np.array_equal(f, want[2])

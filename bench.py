@@ -693,6 +693,7 @@ def run_batched(args):
     (hlf_factor_batched + hlf_enumerate_batched) and against the plain path
     (a factor launch and a reduce launch per grid, matrices staged on the
     device beforehand, no host wait in between)."""
+    import numpy as np
     import torch
 
     from paper_2103_00693_gb300 import autotune
@@ -732,6 +733,23 @@ def run_batched(args):
     e1.record()
     torch.cuda.synchronize()
     split_ms = e0.elapsed_time(e1) / reps
+    # the batched store: every grid's first min(2^r, 2^14) solutions, W words
+    # each, into one buffer at per-grid offsets (an offsets table of B + 1)
+    scap = 1 << 14
+    room = np.minimum(np.left_shift(1, np.clip(r.astype(np.int64), 0, 62)), scap) * B.Ws.astype(np.int64)
+    out_off = np.concatenate([[0], np.cumsum(room)]).astype(np.int64)
+    out_dev = torch.empty(int(out_off[-1]), dtype=torch.int64, device="cuda")
+    out_off_dev = torch.from_numpy(out_off).cuda()
+    B.store(scap, out_dev, out_off_dev)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        B.store(scap, out_dev, out_off_dev)
+    e1.record()
+    torch.cuda.synchronize()
+    store_ms = e0.elapsed_time(e1) / reps
+    store_bytes = int(out_off[-1]) * 8
+    del out_dev
     B.close()
     plain = PlainPath(mats)
     plain.run(cap)  # warm-up: pool, module load
@@ -751,6 +769,12 @@ def run_batched(args):
                          "ops_per_batch": ops, "ops_per_solution": "22W - 4 (18 at W = 1)",
                          "kernel": "batch_kernel", "peak_basis": ipk_basis},
             "split_calls_ms_per_batch": split_ms,
+            "store": {"what": "hlf_enumerate_batched storing min(2^r, 2^14) solutions of every grid",
+                      "ms": store_ms, "bytes": store_bytes,
+                      "roofline": {"bound": "hbm", "achieved": store_bytes / (store_ms / 1e3) / 1e9,
+                                   "peak": peaks()["hbm_gbs"], "unit": "GB/s",
+                                   "frac": store_bytes / (store_ms / 1e3) / 1e9 / peaks()["hbm_gbs"],
+                                   "kernel": "batch_kernel (store chunks)"}},
             "plain_ms_per_batch": plain_ms, "plain_inst_per_s": len(mats) / (plain_ms / 1e3),
             "plain": "per grid: hlf_factor + hlf_enumerate_reduce_upto on one stream, no host wait",
             "speedup_vs_plain": plain_ms / ms}

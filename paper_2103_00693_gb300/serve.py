@@ -165,6 +165,7 @@ class Req:
     ev_factor: object = None
     ev_copy: object = None
     lane: int = 0  # which factor stream
+    packed: np.ndarray | None = None  # the checked, packed rows (set at the first admission attempt)
 
 
 @dataclass
@@ -326,10 +327,12 @@ class Server:
         ended by a host-side check or a failed launch)."""
         import torch
 
-        status, packed = check_request(q)
-        if status:
-            self._finish(q, FAILED, status, st, done, t)
-            return True
+        if q.packed is None:  # checked and packed once, not on every retry while the rings are full
+            status, q.packed = check_request(q)
+            if status:
+                self._finish(q, FAILED, status, st, done, t)
+                return True
+        packed = q.packed
         q.W = hlf.words(q.n)
         nw = q.n * q.W
         if nw > self.in_ring.size or nw > self.mat_ring.size:
@@ -518,6 +521,7 @@ class Server:
                     q.result = self.host_ring.view(q.blk_host, q.count * q.W).numpy().view(np.uint64)\
                         .reshape(q.count, q.W).copy()
                 self._release(q)
+                q.packed = None
                 self._finish(q, OK, 0, st, done, time.perf_counter() - t0)
             if busy_since is not None and not (any(factoring) or pending or copying):
                 st.busy_s += (time.perf_counter() - t0) - busy_since

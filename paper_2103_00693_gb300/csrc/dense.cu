@@ -24,10 +24,11 @@
 // takes the 8-byte aligned outputs this entry point allows).
 //
 // n > 64: 64 solutions of n bits are exactly n words (a group). For n <= 256,
-// dense3_kernel steps whole group blocks by one n-word XOR each (see there).
-// For n > 256, dense2_kernel: a warp produces one group per step, two
-// solutions per lane, each placed with funnel shifts at its bit offset in the
-// group.
+// dense3_kernel steps whole group blocks by one n-word XOR each (see there);
+// it also serves n <= 48 at offsets the lane runs of dense1_kernel do not
+// start on (blocks of 64 * 2^s solutions there). For n > 256, dense2_kernel:
+// a warp produces one group per step, two solutions per lane, each placed
+// with funnel shifts at its bit offset in the group.
 
 #include "enum_impl.cuh"
 
@@ -429,48 +430,53 @@ hlf_status launch_dense2_k(const uint64_t* table, int n, uint64_t offset, uint64
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
-// ------------------------------------------------------------ 64 < n <= 256
-// dense3_kernel walks whole group blocks. Group H holds the solutions
-// 64 H + t, t < 64, and their n-word dense block is
+// ------------------------------------------------------------ block walk
+// dense3_kernel walks whole blocks of G = 64 * 2^s consecutive solutions
+// (s = 0 for 64 < n <= 256; for n < 64, s makes a block K = n * 2^s words,
+// 128 < K <= 256). With m = 6 + s, block H holds the solutions G H + t,
+// t < G, and their K-word dense block is
 //     G(H) = S0 ^ R(D(H)).
-// With g(64 H + t) = (g(H) << 6) ^ ((H & 1) << 5) ^ g(t), solution 64 H + t is
-// Zc(t) ^ D(H), where Zc(t) = z0 ^ XOR_{k in g(t)} B_k (B_0..B_5 only) and
-// D(H) = XOR_{k in (g(H) << 6) ^ ((H & 1) << 5)} B_k. Placing 64 solutions
-// side by side is linear in them, so the block splits into S0, the placement
-// of Zc(0..63) (the same for every group), and R(D(H)), the placement of 64
-// copies of D(H) (the tiling R). D(H + 1) = D(H) ^ C_j with C_j = B_5 ^
-// B_{6+j}, j = ctz(H + 1), so G(H + 1) = G(H) ^ T_j with T_j = R(C_j): one
-// n-word XOR per group.
+// With g(G H + t) = (g(H) << m) ^ ((H & 1) << (m - 1)) ^ g(t), solution
+// G H + t is Zc(t) ^ D(H), where Zc(t) = z0 ^ XOR_{k in g(t)} B_k
+// (B_0..B_{m-1} only) and D(H) = XOR_{k in (g(H) << m) ^ ((H & 1) << (m-1))} B_k.
+// Placing G solutions side by side is linear in them, so the block splits
+// into S0, the placement of Zc(0..G-1) (the same for every block), and
+// R(D(H)), the placement of G copies of D(H) (the tiling R). D(H + 1) =
+// D(H) ^ C_j with C_j = B_{m-1} ^ B_{m+j}, j = ctz(H + 1), so
+// G(H + 1) = G(H) ^ T_j with T_j = R(C_j): one K-word XOR per block.
 //
-// The window [offset, offset + count) starts e = (offset mod 64) n bits into
-// the block of its first group Hw = offset / 64, so stream word p holds bits
+// The window [offset, offset + count) starts e = (offset mod G) n bits into
+// the block of its first group Hw = offset / G, so stream word p holds bits
 // [64 p + e, 64 p + e + 64) of the blocks laid end to end: with e = 64 a + b,
-// word p = k n + q - a comes from group Hw + k as
+// word p = k K + q - a comes from block Hw + k as
 //     G'(H)[q] = f(G(H)[q], G(H)[q + 1]),  f(x, y) = (x >> b) | (y << (64 - b)),
-// where G(H)[n] is word 0 of the next block, G(H + 1)[0]. f is linear too, so
-// the step into group H is G'(H) = G'(H - 1) ^ S_H with
-//     S_H[q] = f(T_j[q], T_j[q + 1]) for q < n - 1,
-//     S_H[n - 1] = f(T_j[n - 1], T_j'[0]),   j = ctz(H), j' = ctz(H + 1).
+// where G(H)[K] is word 0 of the next block, G(H + 1)[0]. f is linear too, so
+// the step into block H is G'(H) = G'(H - 1) ^ S_H with
+//     S_H[q] = f(T_j[q], T_j[q + 1]) for q < K - 1,
+//     S_H[K - 1] = f(T_j[K - 1], T_j'[0]),   j = ctz(H), j' = ctz(H + 1).
 // One of H, H + 1 is odd, so (j, j') is (j, 0) for even H and (0, j') for odd
-// H: the rows S for j, j' < kD3J are kept in shared memory, 2 kD3J rows of n
+// H: the rows S for j, j' < kD3J are kept in shared memory, 2 kD3J rows of K
 // words (all but 1 / 2^kD3J of the steps), and formed on the fly otherwise
 // (b = 0 makes f the identity). Lane l holds the words l + 32 m of G' in
 // registers and stores them straight to global memory, so a warp writes 256
-// consecutive bytes per store instruction and nothing is staged; per 64
-// solutions a lane spends about four instructions per word it owns (load,
-// 64-bit XOR, store).
+// consecutive bytes per store instruction and nothing is staged; per block a
+// lane spends about four instructions per word it owns (load, 64-bit XOR,
+// store).
 constexpr int kD3J = 8;
 constexpr int kD3Threads = 256;
 constexpr int kD3Warps = kD3Threads / 32;
+constexpr int kD3MaxK = 256;  // block words for n < 64
 
 struct Dense3Plan {
-    uint64_t Hw;        // offset / 64: the window's first group
-    uint64_t groups;    // groups the window touches
-    uint64_t per_warp;  // consecutive groups per warp
+    uint64_t Hw;        // offset / G: the window's first block
+    uint64_t groups;    // blocks the window touches
+    uint64_t per_warp;  // consecutive blocks per warp
     uint64_t words;     // ceil(count * n / 64), the stream's length
     uint64_t last_mask; // valid bits of the stream's last word
     uint32_t a, b;      // e = 64 a + b bits of the first block precede the window
-    int n;
+    int n;              // bits per solution
+    int m;              // log2 of the solutions per block (6 + s)
+    int K;              // words per block (n * 2^s)
 };
 
 // Bits [c, c + 64) of the W-word vector x (zero past its last word); x in
@@ -488,14 +494,28 @@ __device__ __forceinline__ uint64_t window64_reg(const uint64_t (&x)[W], uint32_
     return shr64(lo, s) | (s ? shl64(hi, 64 - s) : 0ull);
 }
 
-// Word q of the tiling R(x): 64 copies of the n-bit vector x (shared memory,
-// W words, zero past bit n) side by side. Copy t = 64 q / n starts the word
-// at its bit c = 64 q - t n; when fewer than 64 of its bits remain, the next
-// copy's first bits follow (n > 64, so no word touches three copies).
+// Word q of the tiling R(x): copies of the n-bit vector x (shared memory, W
+// words, zero past bit n) side by side. n > 64: copy t = 64 q / n starts the
+// word at its bit c = 64 q - t n; when fewer than 64 of its bits remain, the
+// next copy's first bits follow (no word touches three copies). n < 64
+// (W = 1): the tiling is periodic with period n, so the word is bits
+// [c, c + 64) of x repeated over 128 bits, c = 64 q mod n.
 template <int W>
 __device__ __forceinline__ uint64_t tile_word(const uint64_t* x, int n, uint32_t q)
 {
-    const uint32_t c = (64u * q) % (uint32_t)n;  // q <= 256: 32-bit arithmetic
+    const uint32_t c = (64u * q) % (uint32_t)n;  // q < 256: 32-bit arithmetic
+    if (W == 1 && n < 64) {
+        uint64_t lo = 0, hi = 0;
+        for (uint32_t at = 0; at < 128; at += (uint32_t)n) {
+            if (at < 64) {
+                lo |= shl64(x[0], at);
+                hi |= at ? shr64(x[0], 64 - at) : 0ull;
+            } else {
+                hi |= shl64(x[0], at - 64);
+            }
+        }
+        return c ? (lo >> c) | (hi << (64 - c)) : lo;
+    }
     const uint32_t w = c >> 6, s = c & 63;
     uint64_t v = shr64(x[w], s);
     if (s && (int)w + 1 < W) v |= shl64(x[w + 1], 64 - s);
@@ -503,10 +523,24 @@ __device__ __forceinline__ uint64_t tile_word(const uint64_t* x, int n, uint32_t
     return v;
 }
 
-// Word q of S0: the placement of Zc(0..63).
+// Word q of S0: the placement of Zc(0..G-1).
 template <int W>
-__device__ __forceinline__ uint64_t group_base_word(const Table<W>& t, int n, uint32_t q)
+__device__ __forceinline__ uint64_t group_base_word(const Table<W>& t, int n, int m, uint32_t q)
 {
+    if (W == 1 && n < 64) {
+        // every solution t whose bits [t n, t n + n) meet [64 q, 64 q + 64)
+        uint64_t v = 0;
+        const uint32_t t0 = (64u * q) / (uint32_t)n, t1 = (64u * q + 63) / (uint32_t)n;
+        for (uint32_t tt = t0; tt <= t1; ++tt) {
+            const uint32_t g = tt ^ (tt >> 1);
+            uint64_t z = t.z0[0];
+            for (int k = 0; k < m; ++k)
+                if ((g >> k) & 1u) z ^= t.B[k][0];
+            const int sh = (int)(tt * (uint32_t)n) - (int)(64u * q);
+            v |= sh >= 0 ? shl64(z, (uint32_t)sh) : shr64(z, (uint32_t)(-sh));
+        }
+        return v;
+    }
     const uint32_t t1 = (64u * q) / (uint32_t)n;
     const uint32_t c = 64 * q - t1 * (uint32_t)n;
     uint64_t a[W];
@@ -532,42 +566,43 @@ __device__ __forceinline__ uint64_t funnel(uint64_t x, uint64_t y, uint32_t b)
 // Word q of the step row S for (j, j'), formed from C_j and C_j' (the rows
 // of rare steps; out of line so that the walk's loops stay unrolled).
 template <int W>
-__device__ __noinline__ uint64_t step_word(const uint64_t* Cj, const uint64_t* Cjn, int n, uint32_t q, uint32_t b)
+__device__ __noinline__ uint64_t step_word(const uint64_t* Cj, const uint64_t* Cjn, int n, int K, uint32_t q,
+                                           uint32_t b)
 {
     const uint64_t x = tile_word<W>(Cj, n, q);
-    return funnel(x, q + 1 < (uint32_t)n ? tile_word<W>(Cj, n, q + 1) : tile_word<W>(Cjn, n, 0), b);
+    return funnel(x, q + 1 < (uint32_t)K ? tile_word<W>(Cj, n, q + 1) : tile_word<W>(Cjn, n, 0), b);
 }
 
-template <int W>
-__global__ void __launch_bounds__(kD3Threads, W == 2 ? 5 : (W == 3 ? 4 : 3)) dense3_kernel(const uint64_t* __restrict__ table, Dense3Plan pl,
-                                                            uint64_t* __restrict__ out)
+// MW: block words per lane (2W for 64 < n <= 256, 8 for n < 64).
+template <int W, int MW>
+__global__ void __launch_bounds__(kD3Threads, W == 3 ? 4 : (W == 4 ? 3 : (MW > 4 ? 4 : 5))) dense3_kernel(
+    const uint64_t* __restrict__ table, Dense3Plan pl, uint64_t* __restrict__ out)
 {
-    constexpr int MW = 2 * W;  // words per lane: 32 lanes x 2W >= n
-    // S rows [2 kD3J][n] (row j: (j, 0), row kD3J + j': (0, j')), S0 [n],
+    // S rows [2 kD3J][K] (row j: (j, 0), row kD3J + j': (0, j')), S0 [K],
     // D [warps][W]
     extern __shared__ __align__(16) uint64_t s_d3[];
     __shared__ Table<W> t;
-    __shared__ uint64_t s_C[kD2Steps][W];  // C_j = B_5 ^ B_{6+j}
-    const int n = pl.n;
+    __shared__ uint64_t s_C[kD2Steps][W];  // C_j = B_{m-1} ^ B_{m+j} (zero past row 64)
+    const int n = pl.n, K = pl.K, mb = pl.m;
     const uint32_t b = pl.b;
     uint64_t* const s_S = s_d3;
-    uint64_t* const s_S0 = s_S + 2 * kD3J * n;
-    uint64_t* const s_D = s_S0 + n;
+    uint64_t* const s_S0 = s_S + 2 * kD3J * K;
+    uint64_t* const s_D = s_S0 + K;
     load_table<W>(t, table);
     __syncthreads();
     for (int i = threadIdx.x; i < kD2Steps * W; i += blockDim.x) {
         const int j = i / W, w = i % W;
-        s_C[j][w] = t.B[5][w] ^ t.B[6 + j][w];
+        s_C[j][w] = mb + j < kTableRows ? t.B[mb - 1][w] ^ t.B[mb + j][w] : 0ull;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * kD3J * n; i += blockDim.x) {
-        const int row = i / n, q = i % n;
+    for (int i = threadIdx.x; i < 2 * kD3J * K; i += blockDim.x) {
+        const int row = i / K, q = i % K;
         const int j = row < kD3J ? row : 0, jn = row < kD3J ? 0 : row - kD3J;
         const uint64_t x = tile_word<W>(s_C[j], n, (uint32_t)q);
-        const uint64_t y = q + 1 < n ? tile_word<W>(s_C[j], n, (uint32_t)q + 1) : tile_word<W>(s_C[jn], n, 0);
+        const uint64_t y = q + 1 < K ? tile_word<W>(s_C[j], n, (uint32_t)q + 1) : tile_word<W>(s_C[jn], n, 0);
         s_S[i] = funnel(x, y, b);
     }
-    for (int q = threadIdx.x; q < n; q += blockDim.x) s_S0[q] = group_base_word<W>(t, n, (uint32_t)q);
+    for (int q = threadIdx.x; q < K; q += blockDim.x) s_S0[q] = group_base_word<W>(t, n, mb, (uint32_t)q);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -575,9 +610,9 @@ __global__ void __launch_bounds__(kD3Threads, W == 2 ? 5 : (W == 3 ? 4 : 3)) den
     const uint64_t k0 = ((uint64_t)blockIdx.x * kD3Warps + warp) * pl.per_warp;
     if (k0 >= pl.groups) return;
     const uint64_t k1 = min(k0 + pl.per_warp, pl.groups);
-    const uint64_t H0 = pl.Hw + k0;  // < 2^58
+    const uint64_t H0 = pl.Hw + k0;  // < 2^(64 - m)
     {  // D(H0): every lane forms it; lane w < W publishes word w
-        uint64_t g = ((H0 ^ (H0 >> 1)) << 6) | ((H0 & 1ull) << 5);
+        uint64_t g = ((H0 ^ (H0 >> 1)) << mb) | ((H0 & 1ull) << (mb - 1));
         uint64_t D[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) D[w] = 0;
@@ -600,74 +635,79 @@ __global__ void __launch_bounds__(kD3Threads, W == 2 ? 5 : (W == 3 ? 4 : 3)) den
         for (int m = 0; m < MW; ++m) {
             const int q = lane + 32 * m;
             uint64_t v = 0;
-            if (q < n) {
+            if (q < K) {
                 v = s_S0[q] ^ tile_word<W>(D, n, (uint32_t)q);
-                if (b) v = funnel(v, q + 1 < n ? s_S0[q + 1] ^ tile_word<W>(D, n, (uint32_t)q + 1) : next0, b);
+                if (b) v = funnel(v, q + 1 < K ? s_S0[q + 1] ^ tile_word<W>(D, n, (uint32_t)q + 1) : next0, b);
             }
             G[m] = v;
         }
     }
-    // groups whose every word lies inside the stream and before its last
-    // word: [ka, kb) (stream word p = k n + q - a of group Hw + k)
-    const uint64_t ka = (pl.a + n - 1) / n;
-    const uint64_t kb = (pl.words + pl.a - 1) / n;  // k n - a + n <= words - 1
-    uint64_t kn = k0 * (uint64_t)n;
-    for (uint64_t k = k0;; kn += n) {
+    // blocks whose every word lies inside the stream and before its last
+    // word: [ka, kb) (stream word p = k K + q - a of block Hw + k)
+    const uint64_t ka = (pl.a + K - 1) / K;
+    const uint64_t kb = (pl.words + pl.a - 1) / K;  // k K - a + K <= words - 1
+    uint64_t kn = k0 * (uint64_t)K;
+    for (uint64_t k = k0;; kn += K) {
         if (k >= ka && k < kb) {
             uint64_t* dst = out + (kn - pl.a);
 #pragma unroll
             for (int m = 0; m < MW; ++m) {
                 const int q = lane + 32 * m;
-                if (q < n) st_cs(dst + q, G[m]);
+                if (q < K) st_cs(dst + q, G[m]);
             }
         } else {
 #pragma unroll
             for (int m = 0; m < MW; ++m) {
                 const int q = lane + 32 * m;
                 const uint64_t p = kn + q - pl.a;  // wraps to a huge value when negative
-                if (q < n && kn + q >= pl.a && p < pl.words)
+                if (q < K && kn + q >= pl.a && p < pl.words)
                     st_cs(out + p, p == pl.words - 1 ? (G[m] & pl.last_mask) : G[m]);
             }
         }
         if (++k == k1) break;
-        const uint64_t H = pl.Hw + k;  // the group stepped to, < 2^58
+        const uint64_t H = pl.Hw + k;  // the block stepped to
         // one of j = ctz(H), j' = ctz(H + 1) is 0: c is the other
         const int c = __ffsll((long long)((H & 1) ? H + 1 : H)) - 1;
         const int row = (H & 1) ? kD3J + c : c;
         if (c < kD3J) {
-            const uint64_t* S = s_S + row * n;
+            const uint64_t* S = s_S + row * K;
 #pragma unroll
             for (int m = 0; m < MW; ++m) {
                 const int q = lane + 32 * m;
-                if (q < n) G[m] ^= S[q];
+                if (q < K) G[m] ^= S[q];
             }
         } else {
 #pragma unroll
             for (int m = 0; m < MW; ++m) {
                 const int q = lane + 32 * m;
-                if (q < n) G[m] ^= step_word<W>(s_C[(H & 1) ? 0 : c], s_C[(H & 1) ? c : 0], n, (uint32_t)q, b);
+                if (q < K) G[m] ^= step_word<W>(s_C[(H & 1) ? 0 : c], s_C[(H & 1) ? c : 0], n, K, (uint32_t)q, b);
             }
         }
     }
 }
 
-template <int W>
+template <int W, int MW>
 hlf_status launch_dense3(const uint64_t* table, int n, uint64_t offset, uint64_t count, uint64_t* out,
                          cudaStream_t s)
 {
     Dense3Plan pl{};
     pl.n = n;
-    pl.Hw = offset >> 6;
-    pl.groups = ((offset + (count - 1)) >> 6) - pl.Hw + 1;  // count >= 1; offset + count - 1 < 2^64
-    const uint64_t bits = count * (uint64_t)n;             // <= 2^64 - 64 (checked by the caller)
+    int sh = 0;  // s: for n < 64 the smallest with n 2^(s+1) > kD3MaxK, so 128 < K <= 256
+    if (n < 64)
+        while ((n << (sh + 1)) <= kD3MaxK) ++sh;
+    pl.m = 6 + sh;
+    pl.K = n << sh;
+    pl.Hw = offset >> pl.m;
+    pl.groups = ((offset + (count - 1)) >> pl.m) - pl.Hw + 1;  // count >= 1; offset + count - 1 < 2^64
+    const uint64_t bits = count * (uint64_t)n;                // <= 2^64 - 64 (checked by the caller)
     pl.words = (bits + 63) / 64;
     pl.last_mask = (bits & 63) ? (1ull << (bits & 63)) - 1 : ~0ull;
-    const uint64_t e = (offset & 63) * (uint64_t)n;
+    const uint64_t e = (offset & ((1ull << pl.m) - 1)) * (uint64_t)n;
     pl.a = (uint32_t)(e >> 6);
     pl.b = (uint32_t)(e & 63);
-    const size_t smem = ((size_t)(2 * kD3J + 1) * n + (size_t)kD3Warps * W) * sizeof(uint64_t);  // <= 34.3 KB
+    const size_t smem = ((size_t)(2 * kD3J + 1) * pl.K + (size_t)kD3Warps * W) * sizeof(uint64_t);  // <= 34.9 KB
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense3_kernel<W>, kD3Threads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense3_kernel<W, MW>, kD3Threads, smem) != cudaSuccess)
         return HLF_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
     const uint64_t max_warps = (uint64_t)sm_count() * per_sm * kD3Warps;
@@ -675,7 +715,7 @@ hlf_status launch_dense3(const uint64_t* table, int n, uint64_t offset, uint64_t
     pl.per_warp = (pl.groups + warps - 1) / warps;
     const uint64_t used = (pl.groups + pl.per_warp - 1) / pl.per_warp;
     const unsigned blocks = (unsigned)((used + kD3Warps - 1) / kD3Warps);
-    dense3_kernel<W><<<blocks, kD3Threads, smem, s>>>(table, pl, out);
+    dense3_kernel<W, MW><<<blocks, kD3Threads, smem, s>>>(table, pl, out);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
@@ -686,7 +726,7 @@ hlf_status launch_dense2(const uint64_t* table, int n, uint64_t offset, uint64_t
                          cudaStream_t s)
 {
     if constexpr (W <= 4) {
-        return launch_dense3<W>(table, n, offset, count, out, s);
+        return launch_dense3<W, 2 * W>(table, n, offset, count, out, s);
     } else {
         if (reinterpret_cast<uintptr_t>(out) % 16 == 0 && n % 2 == 0)
             return launch_dense2_k<W, true, 1>(table, n, offset, count, out, s);
@@ -704,6 +744,12 @@ hlf_status launch_store_dense(const uint64_t* table, int n, uint64_t offset, uin
         const int m = 64 / (n & -n);  // 64 / gcd(n, 64)
         const int M = m < 16 ? 16 : m;
         const bool aligned = (offset & (uint64_t)(M - 1)) == 0;
+        // Offsets that are not a multiple of M: the lane runs then need a
+        // per-lane step table, and 4 GB windows measured 4.4-5.8 TB/s at
+        // n = 33..48 against 6.2 TB/s for the block walk at any offset;
+        // from n = 56 the runs stay ahead (6.6 against 6.2 TB/s), as they do
+        // at aligned offsets (6.2-6.5 TB/s).
+        if (!aligned && n <= 48) return launch_dense3<1, 8>(table, n, offset, count, out, s);
         switch (M) {
         case 16: return aligned ? launch_dense1<16, true>(table, n, offset, count, out, s)
                                 : launch_dense1<16, false>(table, n, offset, count, out, s);

@@ -216,3 +216,46 @@ def test_dense_group_blocks_any_offset(cuda_ok, n):
             assert np.all(got[lead + words:] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote past the stream"
             assert np.all(got[:lead] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote before the stream"
     G.close()
+
+
+@pytest.mark.parametrize("n", [5, 17, 33, 36, 40, 47])
+def test_dense_blocks_small_n_any_offset(cuda_ok, n):
+    """n <= 48 at offsets that are not a multiple of the lane-run length:
+    blocks of 64 * 2^s solutions (n 2^s words, 128 < n 2^s <= 256), the
+    window's shift folded into the step rows. Windows inside one block,
+    across one boundary and many, across large powers of two (rows formed on
+    the fly) and up to the end of the index space; 8- and 16-byte aligned
+    outputs; the whole stream against the oracle, nothing written around it."""
+    import torch
+
+    A = synth.random_symmetric(n, 0.5, 970 + n)
+    F = oc.factor(A)
+    lg = F.space_log2()
+    space = 1 << lg
+    s = 0
+    while (n << (s + 1)) <= 256:
+        s += 1
+    G = 64 << s
+    cases = []
+    for o in (1, 3, G // 2 + 1, G - 1):
+        for off, cnt in ((o, 1), (o, G - o), (o, G - o + 1), (3 * G + o, 5 * G + 11), (o, 70001)):
+            if off + cnt <= space:
+                cases.append((off, cnt))
+        for k in (lg - 3, lg - 1):
+            off = (1 << k) - 4 * G + o
+            if k > 0 and off > 0 and off + 8 * G + 3 <= space:
+                cases.append((off, 8 * G + 3))
+        if space - 2 * G - o > 0:
+            cases.append((space - 2 * G - o, 2 * G + o))
+    assert cases
+    H = hlf.Factorization.from_dense(A)
+    for off, cnt in cases:
+        words = hlf.dense_words(cnt, n)
+        for lead in (0, 1):
+            buf = torch.full((words + 3,), -1, dtype=torch.int64, device="cuda")
+            H.store_dense(off, cnt, buf[lead:])
+            got = buf.cpu().numpy().view(np.uint64)
+            assert np.array_equal(got[lead:lead + words], oc.window_dense(F, off, cnt)), (n, off, cnt, lead)
+            assert np.all(got[lead + words:] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote past the stream"
+            assert np.all(got[:lead] == np.uint64(0xFFFFFFFFFFFFFFFF)), "wrote before the stream"
+    H.close()

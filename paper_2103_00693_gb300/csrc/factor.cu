@@ -7,27 +7,41 @@
 // n > 512 (W >= 9): the same results from two launches that spread the work
 // that does not have to be sequential over many SMs:
 //   factor_elim_kernel   CTA 0 runs the Gauss-Jordan elimination (step (1))
-//                        with the rows of A in registers, by factor_block's
-//                        loop; CTAs 1.. check the input (padding bits,
-//                        symmetry by 64 x 64 bit-block transposes) at the
-//                        same time, each writing its own status slot.
+//                        with the rows of A in registers, in panels of 32
+//                        columns (eliminate_only); CTAs 1.. check the input
+//                        (padding bits, symmetry by 64 x 64 bit-block
+//                        transposes) at the same time, each writing its own
+//                        status slot.
 //   factor_kvec_kernel   one warp per free column f across the GPU: the
 //                        kernel vector x_f, q(x_f) mod 4 and the bit z^a_f
 //                        (steps (2)-(4)), the paper-order table, and, in
 //                        the last CTA to finish, the status and rank.
-// At n = 1024 (grid 32 x 32) this takes 355 us against 392 us in one CTA; at
-// n = 484 the second launch costs more than it saves (143 us against 124 us),
-// hence the threshold.
+// At n = 1024 (grid 32 x 32) this takes 334 us; one CTA running
+// factor_block's column loop for everything took 392 us. At n = 484 the
+// second launch costs more than it saves (143 us against 124 us), hence the
+// threshold.
 //
-// The elimination itself stays one barrier per pivot column. Measured at
-// n = 1024 and dropped:
+// Where the elimination's time goes at n = 1024 (random symmetric, full
+// rank; clock64 phase counters, 667k cycles): the pivot search 365k (356
+// cycles a column), the inversions 127k, the table updates 158k, the tables
+// 26k. The search is one CTA barrier per column and is bound by the issue of
+// its 16 warps: each column costs every warp its candidate, two warp
+// minima, the exchange and the slice updates. Measured at n = 1024 and
+// dropped:
+//   - factor_block's loop (every row's full row XORs the pivot row each
+//     column, 600 cycles a column): 355 us;
 //   - a split barrier (an mbarrier whose arrive precedes the XOR of the
 //     previous pivot row's later words, and whose wait follows it): 607 us;
-//   - panels of 8 columns (a Four-Russians scheme: the pivot search on 8-bit
-//     slices with a mask of the panel's pivots, then one XOR of a table of
-//     pivot-row combinations per row and panel): 367 us with all warps
-//     searching, 431 us with one warp searching bit-planes; the barrier and
-//     the per-column chain dominate, not the XOR volume.
+//   - panels of 8 columns searched on 8-bit slices: 367 us;
+//   - panels of 64 columns with 64-bit slices and a per-row record of the
+//     absorbed pivots instead of the inversion: 395 us;
+//   - two columns per barrier (each warp offering its lowest rows with bit
+//     0, with bit 1 and with bit 0 xor bit 1 set, which settles the pivots
+//     of both columns): 345 us, the search 405 cycles a column;
+//   - a thread-block cluster sharing the rows: its barrier alone takes about
+//     400 cycles a round trip on this GPU (any cluster size), and a
+//     publish-then-minimum exchange over 8 CTAs about 800, more than the
+//     whole column step in one CTA.
 
 #include "factor_impl.cuh"
 
@@ -63,7 +77,7 @@ hlf_status launch_factor_w(const uint64_t* A, int n, const FactorOut& o, cudaStr
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
-// ------------------------------------------------------------ n > 256
+// ------------------------------------------------------------ n > 512
 
 constexpr int kChkCtas = 8;       // CTAs that check the input beside the elimination
 constexpr int kWorkR = 16;        // work[16] = r
@@ -71,10 +85,35 @@ constexpr int kWorkInternal = 17; // work[17] = HLF_ERR_INTERNAL if some q(x_f) 
 constexpr int kWorkDone = 18;     // work[18] = CTAs of factor_kvec_kernel done
 static_assert(kChkCtas <= kWorkR, "one status slot per checking CTA");
 
+// Transpose a 32 x 32 bit block held by one warp: lane l has row l, bit s of
+// a row being column s. Stage j (j = 16, ..., 1) exchanges the bits at column
+// s + j of row t with those at column s of row t + j, for s and t with bit j
+// clear (lanes l and l ^ j pair up); the five stages compose to the transpose.
+__device__ __forceinline__ uint32_t transpose32_warp(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                         : j == 2  ? 0x33333333u : 0x55555555u;
+        const bool upper = (lane & j) != 0;
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, x, j);
+        const uint32_t t = upper ? (((o >> j) ^ x) & m) : (((x >> j) ^ o) & m);
+        x ^= upper ? t : t << j;
+    }
+    return x;
+}
+
 template <int W, int NW>
 struct ElimSmem {
-    int first[2][NW];         // per warp: its lowest candidate's key, by column parity
-    uint64_t crow[2][NW][W];  // and that row's words
+    int first[2][32];          // per warp: its lowest candidate's key, by column parity
+    uint32_t cw[2][32];        // and that row's current slice
+    uint32_t st_piv[32];       // the panel's pivot rows' slices at the panel's start
+    uint32_t H[32];            // their inverse on the pivot columns, over pivot indices
+    int colidx[32];            // pivot index of each column of the panel, -1 if free
+    signed char rowpiv[HLF_MAX_N];  // pivot index of each row in the panel, -1 otherwise
+    uint32_t T1[8 * 16];       // coefficient tables over the start slice's nibbles
+    uint64_t piv[32][W];       // the pivot rows at the panel's start
+    uint64_t T2[8 * 16 * (W | 1)];  // their combinations over 4 pivot indices, odd stride
     int pivcol[HLF_MAX_N];
 };
 
@@ -85,8 +124,8 @@ constexpr size_t elim_smem_bytes(int n)
 }
 
 // Step (1) for the whole CTA: the reduced row echelon form, pivots and the
-// enumeration table, by factor_block's elimination loop; the kernel-vector
-// step and the input checks are left to the other CTAs and kernel. Also
+// enumeration table, by panels of 32 columns (below); the kernel-vector step
+// and the input checks are left to the other CTAs and kernel. Also
 // zeroes the z^a rows of both tables (factor_kvec_kernel ORs the bits in) and
 // the scratch words the second kernel uses, and publishes r in work[kWorkR].
 template <int W, int R, int NW>
@@ -102,7 +141,6 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
     const int bs = blockDim.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const int nwarps = bs >> 5;
 
     uint64_t row[R][W];
 #pragma unroll
@@ -111,65 +149,185 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
 #pragma unroll
         for (int w = 0; w < W; ++w) row[j][w] = i < n ? A[(size_t)i * W + w] : 0ull;
     }
+    // key = (row << 5) | warp; the rows past n are never candidates
+    constexpr int kNever = kNone - 1;
+    int key[R];
     bool used[R];
     int my_k[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
+        key[j] = tid + j * bs < n ? (((tid + j * bs) << 5) | warp) : kNever;
         used[j] = false;
         my_k[j] = -1;
     }
+    if (tid < 64) (&sm.first[0][0])[tid] = kNone;  // the slots of absent warps stay empty
+    for (int i = tid; i < HLF_MAX_N; i += bs) sm.rowpiv[i] = -1;
+    __syncthreads();
+
+    // Panels of 32 columns. (a) Pivot search on the rows' 32-bit slices: for
+    // each column the lowest unused row with the bit becomes the pivot and
+    // every slice with the bit absorbs the pivot's (the pivot's own slice
+    // turns to zero, so it is never a candidate again); the slices rotate
+    // so that bit 0 is the column. (b) One warp inverts the pivots' start
+    // slices restricted to the pivot columns: row k of the inverse (H_k)
+    // says which pivot start rows XOR to the fully reduced pivot row k.
+    // (c) Every row is rebuilt from the panel's start values: a pivot row
+    // as the XOR of the start rows in H_k, any other row as itself XOR the
+    // reduced pivot rows of the pivot columns its start slice has, whose
+    // start-row combination is read from nibble tables of H (T1). The
+    // result has zeros on the panel's pivot columns and spans the same rows,
+    // so it is the Gauss-Jordan elimination of the panel; the pivot rows are
+    // zero left of the panel, so only words w.. change.
     int rank = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-        for (int b = 0; b < 64; ++b) {
-            const int c = (w << 6) + b;
-            if (c >= n) break;
-            const int buf = c & 1;
-            int cand = kNone;
 #pragma unroll
-            for (int j = R - 1; j >= 0; --j)
-                if (tid + j * bs < n && !used[j] && ((row[j][w] >> b) & 1ull)) cand = ((tid + j * bs) << 5) | warp;
-            const int wmin = __reduce_min_sync(0xffffffffu, cand);
-            if (wmin != kNone && cand == wmin) {
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    if (tid + j * bs != (wmin >> 5)) continue;
-#pragma unroll
-                    for (int v = w; v < W; ++v) sm.crow[buf][warp][v] = row[j][v];
-                }
-            }
-            if (lane == 0) sm.first[buf][warp] = wmin;
-            __syncthreads();
-            int pk = lane < nwarps ? sm.first[buf][lane] : kNone;
-            pk = __reduce_min_sync(0xffffffffu, pk);
-            if (pk == kNone) continue;  // no pivot in column c (uniform)
-            const uint64_t* prow = sm.crow[buf][pk & 31];
-            const int p = pk >> 5;
+        for (int h = 0; h < 2; ++h) {
+            const int c0 = (w << 6) + (h << 5);
+            if (c0 >= n) break;
+            const int ncols = n - c0 < 32 ? n - c0 : 32;
+            uint32_t st[R], s[R];
+            int my_kp[R];
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                if (tid + j * bs == p) {
-                    used[j] = true;
-                    my_k[j] = rank;
-                }
+                st[j] = (uint32_t)(row[j][w] >> (32 * h));
+                s[j] = used[j] ? 0u : st[j];
+                my_kp[j] = -1;
             }
-            if (tid == 0) sm.pivcol[rank] = c;
-            if constexpr (R == 1) {  // row p; its words below word w are zero
-                uint64_t pv[W];
+            if (tid < 32) sm.colidx[tid] = -1;  // read last before the previous panel's update barrier
+            int kp = 0;
+            // rolled: 2W copies of the panel code suit the instruction
+            // cache, 64W copies of this body would not
+#pragma unroll 1
+            for (int b = 0; b < ncols; ++b) {
+                const int buf = b & 1;
+                int cand = kNone;
 #pragma unroll
-                for (int v = w; v < W; ++v) pv[v] = prow[v];
-                const uint64_t m = (tid != p && ((row[0][w] >> b) & 1ull)) ? ~0ull : 0ull;
+                for (int j = 0; j < R; ++j) cand = min(cand, (s[j] & 1u) ? key[j] : kNone);
+                const int wmin = __reduce_min_sync(0xffffffffu, cand);
+                if (cand == wmin && wmin != kNone) {  // the lane of the warp's candidate
+                    uint32_t sv = s[0];
 #pragma unroll
-                for (int v = w; v < W; ++v) row[0][v] ^= pv[v] & m;
-            } else {
+                    for (int j = 1; j < R; ++j) sv = cand == key[j] ? s[j] : sv;
+                    sm.cw[buf][warp] = sv;
+                }
+                if (lane == 0) sm.first[buf][warp] = wmin;
+                __syncthreads();
+                const int pk = __reduce_min_sync(0xffffffffu, sm.first[buf][lane]);
+                // no row has bit 0 set when the column has no pivot
+                const uint32_t ps = pk != kNone ? sm.cw[buf][pk & 31] : 0u;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    if (tid + j * bs != p && ((row[j][w] >> b) & 1ull)) {
-#pragma unroll
-                        for (int v = w; v < W; ++v) row[j][v] ^= prow[v];
+                    const uint32_t t = (s[j] & 1u) ? s[j] ^ ps : s[j];
+                    s[j] = __funnelshift_r(t, t, 1);
+                }
+                if (pk != kNone) {  // uniform
+                    if (tid == 0) {
+                        sm.colidx[b] = kp;
+                        sm.pivcol[rank + kp] = c0 + b;
+                        sm.rowpiv[pk >> 5] = (signed char)kp;
                     }
+                    ++kp;
                 }
             }
-            ++rank;
+            __syncthreads();  // rowpiv complete
+            // the pivot rows: start slice and start row (words w..) to the tables
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (key[j] == kNever) continue;
+                const int k = sm.rowpiv[tid + j * bs];
+                if (k < 0) continue;
+                sm.rowpiv[tid + j * bs] = -1;
+                my_kp[j] = k;
+                used[j] = true;
+                my_k[j] = rank + k;
+                sm.st_piv[k] = st[j];
+#pragma unroll
+                for (int v = w; v < W; ++v) sm.piv[k][v] = row[j][v];
+            }
+            rank += kp;
+            __syncthreads();
+            if (kp == 0) continue;  // uniform
+            const int V = W - w;
+            const int VP = V | 1;  // odd stride: the 16 entries of a table in distinct banks
+            if (warp == 0) {
+                // (b) Gauss-Jordan of the kp start slices on the pivot
+                // columns, held by columns: lane c has column c of the
+                // slices (bit k = slice k's bit c) and column c of the
+                // augmented identity. A step reads one column by a shuffle;
+                // the row it picks and the rows it changes are then known to
+                // every lane, each updating its own column.
+                const int ci = sm.colidx[lane];
+                const unsigned pmask = __ballot_sync(0xffffffffu, ci >= 0);
+                uint32_t col = transpose32_warp(lane < kp ? sm.st_piv[lane] : 0u, lane);
+                uint32_t hcol = lane < kp ? (1u << lane) : 0u;
+                uint32_t done = 0u;   // rows already holding a pivot column
+                uint32_t mybit = 1u;  // lane b: the row that holds pivot column b, as a bit
+#pragma unroll
+                for (int b = 0; b < 32; ++b) {  // branch-free: a free column picks no row
+                    const uint32_t colb = __shfl_sync(0xffffffffu, col, b);
+                    const uint32_t cand = colb & ~done & (0u - ((pmask >> b) & 1u));
+                    const uint32_t lb = cand & (0u - cand);  // the lowest such row
+                    done |= lb;
+                    if (lane == b && lb) mybit = lb;
+                    const uint32_t rows = colb & ~lb;  // the rows that absorb it
+                    if (col & lb) col ^= rows;
+                    if (hcol & lb) hcol ^= rows;
+                }
+                const int myrow = __ffs(mybit) - 1;
+                // row L of the augmented part, over the pivot indices, is H of
+                // the pivot column L holds
+                const uint32_t hrow = transpose32_warp(hcol, lane);
+                const uint32_t hv = __shfl_sync(0xffffffffu, hrow, myrow);
+                if (ci >= 0) sm.H[ci] = hv;
+            } else {
+                // T2[(t, x)][v]: XOR of the start rows' word w + v of the pivots
+                // 4t + i, i over the bits of x
+                for (int e = tid - 32; e < 128 * V; e += bs - 32) {
+                    const int v = e % V;
+                    const int tx = e / V;
+                    const int k0 = (tx >> 4) << 2;
+                    uint64_t acc = 0ull;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (((tx >> i) & 1) && k0 + i < kp) acc ^= sm.piv[k0 + i][w + v];
+                    sm.T2[tx * VP + v] = acc;
+                }
+            }
+            __syncthreads();
+            if (tid < 128) {  // T1[(t, x)]: XOR of H over the pivot columns 4t + i, i over the bits of x
+                const int t = tid >> 4;
+                uint32_t acc = 0u;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = sm.colidx[4 * t + i];
+                    if (((tid >> i) & 1) && j >= 0) acc ^= sm.H[j];
+                }
+                sm.T1[tid] = acc;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                uint32_t coef;
+                if (my_kp[j] >= 0) {
+                    coef = sm.H[my_kp[j]];
+#pragma unroll
+                    for (int v = w; v < W; ++v) row[j][v] = 0ull;
+                } else {
+                    coef = 0u;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) coef ^= sm.T1[(t << 4) | ((st[j] >> (4 * t)) & 15u)];
+                }
+                const uint64_t* tb[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) tb[t] = sm.T2 + ((t << 4) | (int)((coef >> (4 * t)) & 15u)) * VP;
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    row[j][w + v] ^= ((tb[0][v] ^ tb[1][v]) ^ (tb[2][v] ^ tb[3][v])) ^
+                                     ((tb[4][v] ^ tb[5][v]) ^ (tb[6][v] ^ tb[7][v]));
+            }
+            // the next panel's first column barrier orders these reads before
+            // H, T1 and T2 are written again
         }
     }
     const int r = rank;
@@ -280,9 +438,16 @@ __global__ void __launch_bounds__(256) factor_kvec_kernel(const uint64_t* __rest
         // the paper's order: row l = XOR of A's columns (= rows) at p_{r-1}, .., p_{r-1-l}
         const int nb = r < HLF_MAX_VARYING ? r : HLF_MAX_VARYING;
         uint64_t acc = 0;
-        for (int l = 0; l < nb; ++l) {
-            acc ^= A[(size_t)__ldcg(o.piv + r - 1 - l) * W + lane];
-            o.ptable[l * W + lane] = acc;
+        for (int l0 = 0; l0 < nb; l0 += 8) {  // eight independent loads in flight
+            uint64_t a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                a[u] = l0 + u < nb ? A[(size_t)__ldcg(o.piv + r - 1 - l0 - u) * W + lane] : 0ull;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                acc ^= a[u];
+                if (l0 + u < nb) o.ptable[(l0 + u) * W + lane] = acc;
+            }
         }
     }
 
@@ -294,19 +459,31 @@ __global__ void __launch_bounds__(256) factor_kvec_kernel(const uint64_t* __rest
         const int fb = f & 63;
         if (lane < W) s_x[warp][lane] = lane == fw ? (1ull << fb) : 0ull;
         __syncwarp();
-        // bit p_k of x_f is B_k[f]: each lane sets the bits of its k
-        for (int k = lane; k < r; k += 32) {
-            if ((__ldcg(o.basis + (size_t)k * W + fw) >> fb) & 1ull) {
-                const int pc = __ldcg(o.piv + k);
-                atomicOr(reinterpret_cast<unsigned long long*>(&s_x[warp][pc >> 6]), 1ull << (pc & 63));
+        // bit p_k of x_f is B_k[f]: each lane sets the bits of its k, four
+        // loads in flight
+        for (int k0 = lane; k0 < r; k0 += 128) {
+            uint64_t bk[4];
+            int pc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + 32 * u;
+                bk[u] = k < r ? __ldcg(o.basis + (size_t)k * W + fw) : 0ull;
+                pc[u] = k < r ? __ldcg(o.piv + k) : 0;
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if ((bk[u] >> fb) & 1ull)
+                    atomicOr(reinterpret_cast<unsigned long long*>(&s_x[warp][pc[u] >> 6]), 1ull << (pc[u] & 63));
         }
         __syncwarp();
+        uint64_t xr[W];
+#pragma unroll
+        for (int v = 0; v < W; ++v) xr[v] = s_x[warp][v];
         unsigned acc = 0;
         for (int i = lane; i < n; i += 32) {
             if ((s_x[warp][i >> 6] >> (i & 63)) & 1ull) {
 #pragma unroll
-                for (int v = 0; v < W; ++v) acc += __popcll(A[(size_t)i * W + v] & s_x[warp][v]);
+                for (int v = 0; v < W; ++v) acc += __popcll(A[(size_t)i * W + v] & xr[v]);
             }
         }
         const unsigned q = __reduce_add_sync(0xffffffffu, acc) & 3u;

@@ -12,7 +12,7 @@
 //                        (padding bits, symmetry by 64 x 64 bit-block
 //                        transposes) at the same time, each writing its own
 //                        status slot.
-//   factor_kvec_kernel   one warp per free column f across the GPU: the
+//   factor_kvec_kernel   one CTA per free column f across the GPU: the
 //                        kernel vector x_f, q(x_f) mod 4 and the bit z^a_f
 //                        (steps (2)-(4)), the paper-order table, and, in
 //                        the last CTA to finish, the status and rank.
@@ -83,6 +83,9 @@ constexpr int kChkCtas = 8;       // CTAs that check the input beside the elimin
 constexpr int kWorkR = 16;        // work[16] = r
 constexpr int kWorkInternal = 17; // work[17] = HLF_ERR_INTERNAL if some q(x_f) was odd
 constexpr int kWorkDone = 18;     // work[18] = CTAs of factor_kvec_kernel done
+constexpr int kWorkMask = 32;     // work[32..64) = the pivot columns, one bit each
+constexpr int kKvecCtas = 256;    // CTAs of factor_kvec_kernel (one free column at a time each)
+static_assert(kWorkMask + HLF_MAX_N / 32 <= kFactorWorkWords, "the pivot mask fits the scratch words");
 static_assert(kChkCtas <= kWorkR, "one status slot per checking CTA");
 
 // Transpose a 32 x 32 bit block held by one warp: lane l has row l, bit s of
@@ -103,6 +106,40 @@ __device__ __forceinline__ uint32_t transpose32_warp(uint32_t x, int lane)
     return x;
 }
 
+// Step (b) of a panel, by warp 0: Gauss-Jordan of the kp pivot rows' start
+// slices st_piv on the pivot columns (colidx[b] >= 0), held by columns: lane
+// c has column c of the slices (bit k = slice k's bit c) and column c of the
+// augmented identity. A step reads one column by a shuffle; the row it picks
+// and the rows it changes are then known to every lane, each updating its
+// own column. H[colidx[b]] receives the row of the inverse that yields the
+// reduced pivot row of column b, over the pivot indices. Kept out of line:
+// one copy serves all 2W panels (the instruction cache holds it).
+__device__ __noinline__ void invert_panel(int kp, const uint32_t* st_piv, const int* colidx, uint32_t* H, int lane)
+{
+    const int ci = colidx[lane];
+    const unsigned pmask = __ballot_sync(0xffffffffu, ci >= 0);
+    uint32_t col = transpose32_warp(lane < kp ? st_piv[lane] : 0u, lane);
+    uint32_t hcol = lane < kp ? (1u << lane) : 0u;
+    uint32_t done = 0u;   // rows already holding a pivot column
+    uint32_t mybit = 1u;  // lane b: the row that holds pivot column b, as a bit
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {  // branch-free: a free column picks no row
+        const uint32_t colb = __shfl_sync(0xffffffffu, col, b);
+        const uint32_t cand = colb & ~done & (0u - ((pmask >> b) & 1u));
+        const uint32_t lb = cand & (0u - cand);  // the lowest such row
+        done |= lb;
+        if (lane == b && lb) mybit = lb;
+        const uint32_t rows = colb & ~lb;  // the rows that absorb it
+        if (col & lb) col ^= rows;
+        if (hcol & lb) hcol ^= rows;
+    }
+    // row L of the augmented part, over the pivot indices, is H of the pivot
+    // column L holds
+    const uint32_t hrow = transpose32_warp(hcol, lane);
+    const uint32_t hv = __shfl_sync(0xffffffffu, hrow, __ffs(mybit) - 1);
+    if (ci >= 0) H[ci] = hv;
+}
+
 template <int W, int NW>
 struct ElimSmem {
     int first[2][32];          // per warp: its lowest candidate's key, by column parity
@@ -110,6 +147,7 @@ struct ElimSmem {
     uint32_t st_piv[32];       // the panel's pivot rows' slices at the panel's start
     uint32_t H[32];            // their inverse on the pivot columns, over pivot indices
     int colidx[32];            // pivot index of each column of the panel, -1 if free
+    uint32_t pivmask[HLF_MAX_N / 32];  // the pivot columns, for the second kernel
     signed char rowpiv[HLF_MAX_N];  // pivot index of each row in the panel, -1 otherwise
     uint32_t T1[8 * 16];       // coefficient tables over the start slice's nibbles
     uint64_t piv[32][W];       // the pivot rows at the panel's start
@@ -178,10 +216,14 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
     // result has zeros on the panel's pivot columns and spans the same rows,
     // so it is the Gauss-Jordan elimination of the panel; the pivot rows are
     // zero left of the panel, so only words w.. change.
+    constexpr int kHalvesUnroll = W > 11 ? 2 : 1;
     int rank = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-#pragma unroll
+        // both halves of word w run the same code (the registers it names
+        // depend on w only): rolled, W copies in all, save where the rolled
+        // loop spills (W > 11, measured slower)
+#pragma unroll kHalvesUnroll
         for (int h = 0; h < 2; ++h) {
             const int c0 = (w << 6) + (h << 5);
             if (c0 >= n) break;
@@ -251,35 +293,7 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
             const int V = W - w;
             const int VP = V | 1;  // odd stride: the 16 entries of a table in distinct banks
             if (warp == 0) {
-                // (b) Gauss-Jordan of the kp start slices on the pivot
-                // columns, held by columns: lane c has column c of the
-                // slices (bit k = slice k's bit c) and column c of the
-                // augmented identity. A step reads one column by a shuffle;
-                // the row it picks and the rows it changes are then known to
-                // every lane, each updating its own column.
-                const int ci = sm.colidx[lane];
-                const unsigned pmask = __ballot_sync(0xffffffffu, ci >= 0);
-                uint32_t col = transpose32_warp(lane < kp ? sm.st_piv[lane] : 0u, lane);
-                uint32_t hcol = lane < kp ? (1u << lane) : 0u;
-                uint32_t done = 0u;   // rows already holding a pivot column
-                uint32_t mybit = 1u;  // lane b: the row that holds pivot column b, as a bit
-#pragma unroll
-                for (int b = 0; b < 32; ++b) {  // branch-free: a free column picks no row
-                    const uint32_t colb = __shfl_sync(0xffffffffu, col, b);
-                    const uint32_t cand = colb & ~done & (0u - ((pmask >> b) & 1u));
-                    const uint32_t lb = cand & (0u - cand);  // the lowest such row
-                    done |= lb;
-                    if (lane == b && lb) mybit = lb;
-                    const uint32_t rows = colb & ~lb;  // the rows that absorb it
-                    if (col & lb) col ^= rows;
-                    if (hcol & lb) hcol ^= rows;
-                }
-                const int myrow = __ffs(mybit) - 1;
-                // row L of the augmented part, over the pivot indices, is H of
-                // the pivot column L holds
-                const uint32_t hrow = transpose32_warp(hcol, lane);
-                const uint32_t hv = __shfl_sync(0xffffffffu, hrow, myrow);
-                if (ci >= 0) sm.H[ci] = hv;
+                invert_panel(kp, sm.st_piv, sm.colidx, sm.H, lane);
             } else {
                 // T2[(t, x)][v]: XOR of the start rows' word w + v of the pivots
                 // 4t + i, i over the bits of x
@@ -352,6 +366,11 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
         if (o.ptable) o.ptable[i] = 0ull;
     }
     for (int k = tid; k < r; k += bs) o.piv[k] = sm.pivcol[k];
+    if (tid < HLF_MAX_N / 32) sm.pivmask[tid] = 0u;
+    __syncthreads();
+    for (int k = tid; k < r; k += bs) atomicOr(&sm.pivmask[sm.pivcol[k] >> 5], 1u << (sm.pivcol[k] & 31));
+    __syncthreads();
+    if (tid < HLF_MAX_N / 32) o.work[kWorkMask + tid] = (int32_t)sm.pivmask[tid];
     if (tid == 0) {
         o.work[kWorkR] = r;
         o.work[kWorkInternal] = 0;
@@ -410,31 +429,43 @@ __global__ void __launch_bounds__(512, 1) factor_elim_kernel(const uint64_t* __r
     eliminate_only<W, rows_per_thread<W>(), 16>(A, n, o, smem);
 }
 
-// Steps (2)-(4), one warp per free column f: x_f = e_f + sum_k B_k[f] e_{p_k},
+// Steps (2)-(4), one CTA per free column f (the j-th free column, j =
+// blockIdx.x, blockIdx.x + gridDim.x, ..., found from the pivot mask the
+// elimination left in the scratch words): x_f = e_f + sum_k B_k[f] e_{p_k},
 // q(x_f) = sum over i in supp(x_f) of popcount(A_i & x_f) mod 4, and
-// z^a_f = q(x_f) / 2 (z^a vanishes on the pivots). The paper-order table is
-// built by warp 0 of CTA 0, as in factor_block. The last CTA to finish folds
-// the checking CTAs' verdicts and the q parity into the status word.
+// z^a_f = q(x_f) / 2 (z^a vanishes on the pivots). Each thread takes every
+// 256th k and every 256th row, so a free column costs a few rounds of
+// memory latency, not one per row. The paper-order table is built by warp 1
+// of CTA 0, as in factor_block. The last CTA to finish folds the checking
+// CTAs' verdicts and the q parity into the status word.
 template <int W>
 __global__ void __launch_bounds__(256) factor_kvec_kernel(const uint64_t* __restrict__ A, int n, FactorOut o,
                                                           int n_chk)
 {
-    constexpr int NW = 8;
-    __shared__ uint32_t s_pivmask[HLF_MAX_N / 32];
-    __shared__ uint64_t s_x[NW][W];
+    __shared__ uint32_t s_mask[HLF_MAX_N / 32];  // free columns below n, by word
+    __shared__ int s_before[HLF_MAX_N / 32];     // free columns in the words before
+    __shared__ uint64_t s_x[W];
+    __shared__ unsigned s_q;
     __shared__ bool s_last;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
     const int r = __ldcg(o.work + kWorkR);
-    for (int i = threadIdx.x; i < HLF_MAX_N / 32; i += blockDim.x) s_pivmask[i] = 0;
-    __syncthreads();
-    for (int k = threadIdx.x; k < r; k += blockDim.x) {
-        const int c = __ldcg(o.piv + k);
-        atomicOr(&s_pivmask[c >> 5], 1u << (c & 31));
+    if (warp == 0) {
+        const int c0 = lane * 32;
+        const uint32_t below_n = c0 >= n ? 0u : (n - c0 >= 32 ? ~0u : ((1u << (n - c0)) - 1u));
+        const uint32_t fm = ~(uint32_t)__ldcg(o.work + kWorkMask + lane) & below_n;
+        const int cnt = __popc(fm);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        s_mask[lane] = fm;
+        s_before[lane] = incl - cnt;
     }
-    __syncthreads();
-
-    if (blockIdx.x == 0 && warp == 0 && o.ptable && lane < W) {
+    if (blockIdx.x == 0 && warp == 1 && o.ptable && lane < W) {
         // the paper's order: row l = XOR of A's columns (= rows) at p_{r-1}, .., p_{r-1-l}
         const int nb = r < HLF_MAX_VARYING ? r : HLF_MAX_VARYING;
         uint64_t acc = 0;
@@ -450,59 +481,76 @@ __global__ void __launch_bounds__(256) factor_kvec_kernel(const uint64_t* __rest
             }
         }
     }
+    __syncthreads();
 
     int err = 0;
-    const int gw = blockIdx.x * NW + warp;
-    for (int f = gw; f < n; f += gridDim.x * NW) {
-        if ((s_pivmask[f >> 5] >> (f & 31)) & 1u) continue;  // pivot column (uniform per warp)
+    const int nfree = n - r;
+    for (int j = blockIdx.x; j < nfree; j += gridDim.x) {
+        // the j-th free column: the last mask word with at most j free
+        // columns before it holds it
+        const int l = 31 - __clz(__ballot_sync(0xffffffffu, s_before[lane] <= j));
+        uint32_t m = s_mask[l];
+        for (int t = j - s_before[l]; t > 0; --t) m &= m - 1u;
+        if (!m) continue;  // not reached: the mask has n - r free columns (uniform)
+        const int f = 32 * l + __ffs(m) - 1;
         const int fw = f >> 6;
         const int fb = f & 63;
-        if (lane < W) s_x[warp][lane] = lane == fw ? (1ull << fb) : 0ull;
-        __syncwarp();
-        // bit p_k of x_f is B_k[f]: each lane sets the bits of its k, four
-        // loads in flight
-        for (int k0 = lane; k0 < r; k0 += 128) {
+        if (tid < W) s_x[tid] = tid == fw ? (1ull << fb) : 0ull;
+        if (tid == 0) s_q = 0u;
+        __syncthreads();
+        // bit p_k of x_f is B_k[f]: thread t sets the bits of k = t, t + 256, ...
+        for (int k0 = tid; k0 < r; k0 += 1024) {  // four loads in flight
             uint64_t bk[4];
             int pc[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int k = k0 + 32 * u;
+                const int k = k0 + 256 * u;
                 bk[u] = k < r ? __ldcg(o.basis + (size_t)k * W + fw) : 0ull;
                 pc[u] = k < r ? __ldcg(o.piv + k) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if ((bk[u] >> fb) & 1ull)
-                    atomicOr(reinterpret_cast<unsigned long long*>(&s_x[warp][pc[u] >> 6]), 1ull << (pc[u] & 63));
+                    atomicOr(reinterpret_cast<unsigned long long*>(&s_x[pc[u] >> 6]), 1ull << (pc[u] & 63));
         }
-        __syncwarp();
+        __syncthreads();
         uint64_t xr[W];
 #pragma unroll
-        for (int v = 0; v < W; ++v) xr[v] = s_x[warp][v];
+        for (int v = 0; v < W; ++v) xr[v] = s_x[v];
         unsigned acc = 0;
-        for (int i = lane; i < n; i += 32) {
-            if ((s_x[warp][i >> 6] >> (i & 63)) & 1ull) {
+        for (int i0 = tid; i0 < n; i0 += 512) {  // two rows' loads in flight
+            const int i1 = i0 + 256;
+            const bool in0 = (s_x[i0 >> 6] >> (i0 & 63)) & 1ull;
+            const bool in1 = i1 < n && ((s_x[i1 >> 6] >> (i1 & 63)) & 1ull);
 #pragma unroll
-                for (int v = 0; v < W; ++v) acc += __popcll(A[(size_t)i * W + v] & xr[v]);
+            for (int v = 0; v < W; ++v) {
+                const uint64_t a0 = in0 ? A[(size_t)i0 * W + v] : 0ull;
+                const uint64_t a1 = in1 ? A[(size_t)i1 * W + v] : 0ull;
+                acc += __popcll(a0 & xr[v]) + __popcll(a1 & xr[v]);
             }
         }
-        const unsigned q = __reduce_add_sync(0xffffffffu, acc) & 3u;
-        if (q & 1u) err = HLF_ERR_INTERNAL;  // q is even on Ker(A) for symmetric A
-        if (lane == 0 && (q >> 1)) {
-            atomicOr(reinterpret_cast<unsigned long long*>(o.table + kTableZ0Row * W + fw), 1ull << fb);
-            if (o.ptable)
-                atomicOr(reinterpret_cast<unsigned long long*>(o.ptable + kTableZ0Row * W + fw), 1ull << fb);
+        acc = __reduce_add_sync(0xffffffffu, acc);
+        if (lane == 0) atomicAdd(&s_q, acc);
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned q = s_q & 3u;
+            if (q & 1u) err = HLF_ERR_INTERNAL;  // q is even on Ker(A) for symmetric A
+            if (q >> 1) {
+                atomicOr(reinterpret_cast<unsigned long long*>(o.table + kTableZ0Row * W + fw), 1ull << fb);
+                if (o.ptable)
+                    atomicOr(reinterpret_cast<unsigned long long*>(o.ptable + kTableZ0Row * W + fw), 1ull << fb);
+            }
         }
-        __syncwarp();
+        __syncthreads();  // s_x and s_q serve the next free column
     }
     if (err) atomicMax(o.work + kWorkInternal, err);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         __threadfence();
         s_last = atomicAdd(o.work + kWorkDone, 1) == (int)gridDim.x - 1;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last && tid == 0) {
         __threadfence();
         // an input fault first (as factor_block reports it), then an odd q
         int st = 0;
@@ -531,9 +579,7 @@ hlf_status launch_factor_large(const uint64_t* A, int n, const FactorOut& o, cud
     }
     factor_elim_kernel<W><<<1 + kChkCtas, threads, smem, s>>>(A, n, o);
     if (cudaGetLastError() != cudaSuccess) return HLF_ERR_CUDA;
-    // one warp per free column at most: n warps over CTAs of 8
-    const int blocks = (n + 7) / 8;
-    factor_kvec_kernel<W><<<blocks, 256, 0, s>>>(A, n, o, kChkCtas);
+    factor_kvec_kernel<W><<<kKvecCtas, 256, 0, s>>>(A, n, o, kChkCtas);
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 

@@ -35,6 +35,22 @@ def test_served_equals_alone_and_oracle(cuda_ok):
         assert np.array_equal(q.result, oc.window(F, off, cnt)), q.id
 
 
+def test_sparse_stream_equals_plain_and_oracle(cuda_ok):
+    """A sparse stream (the server idle between most arrivals, one request
+    per tick): every result equals the plain path and the oracle."""
+    reqs = _stream(24, 300.0, 11)
+    srv = serve.Server(device_bytes=64 << 20, host_bytes=64 << 20)
+    st, done = srv.run(reqs)
+    srv.close()
+    assert len(done) == len(reqs) and all(q.outcome == "ok" for q in done)
+    _, alone = serve.run_plain(reqs)
+    by_id = {q.id: q for q in alone}
+    for q in done:
+        assert np.array_equal(q.result, by_id[q.id].result), q.id
+        F = oc.factor(q.A)
+        assert np.array_equal(q.result, oc.window(F, q.offset, q.count)), q.id
+
+
 def test_served_under_tight_memory_budget(cuda_ok):
     """A budget that fits only a few windows at once still serves everything
     exactly (requests wait for admission)."""
@@ -63,14 +79,14 @@ def test_served_large_windows_mixed_sizes(cuda_ok):
         assert np.array_equal(q.result, by_id[q.id].result)
 
 
-def _planted_stream(seed=21):
+def _planted_stream(seed=21, rate=4000.0):
     """A Poisson stream with malformed, oversized and cancelled requests
     planted among good ones. Returns (stream, expected outcome by id, ids to
     cancel at admission, ids to cancel once factored, ids whose factor call
     gets an injected allocation failure)."""
     import paper_2103_00693_gb300 as hlf
 
-    reqs = _stream(70, 4000.0, seed)
+    reqs = _stream(70, rate, seed)
     expect = {}
     # requests 0 and 1 reach hlf_factor first: their allocations are failed
     nomem = [0, 1]
@@ -108,7 +124,8 @@ def _planted_stream(seed=21):
     return reqs, expect, at_admit, at_factored, nomem
 
 
-def test_served_failures_and_cancellations(cuda_ok):
+@pytest.mark.parametrize("rate", [4000.0, 300.0], ids=["busy", "idle"])
+def test_served_failures_and_cancellations(cuda_ok, rate):
     """Malformed, oversized, cancelled and allocation-failed requests in a
     Poisson stream each end alone with their status; every other result is
     bit-exact against the oracle; the rings are empty afterwards and the
@@ -117,7 +134,7 @@ def test_served_failures_and_cancellations(cuda_ok):
     own device status word."""
     import paper_2103_00693_gb300 as hlf
 
-    reqs, expect, at_admit, at_factored, nomem = _planted_stream()
+    reqs, expect, at_admit, at_factored, nomem = _planted_stream(rate=rate)
     srv = serve.Server(device_bytes=64 << 20, host_bytes=64 << 20)
 
     def on_event(kind, q):

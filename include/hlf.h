@@ -97,6 +97,26 @@ int32_t hlf_device_count(void);
  * Process-wide, shared by all threads. */
 hlf_status hlf_debug_fail_allocs(int32_t count);
 
+/* The debug build (the paper has no counterpart; it stands in for a race and
+ * bounds checker that this GPU pool does not offer). Built with -DHLF_DEBUG
+ * (the Python binding loads that library when HLF_DEBUG=1), the kernels test
+ * the index of every solution store against its output buffer and of their
+ * shared-memory tables against the table; an access that would fall outside
+ * is skipped and the first such event recorded on the device.
+ * hlf_debug_violation synchronises the current device, writes that record to
+ * *first and clears it: 0 if none, else 2^63 | site << 48 | (index mod 2^48),
+ * the sites listed in the library's sources (1 = hlf_debug_bounds_probe).
+ * *is_debug is 1 in a debug build, 0 in a release build (where *first is
+ * always 0). HLF_ERR_ARG if a pointer is null; HLF_ERR_CUDA if the device
+ * cannot be read. */
+hlf_status hlf_debug_violation(uint64_t* first, int32_t* is_debug);
+
+/* A check of the check: one device thread tests index i against [0, n) at
+ * site 1 and touches no memory, so a test can see a failed check recorded
+ * (debug build) or not (release build). Asynchronous on stream (a
+ * cudaStream_t, 0 for the legacy stream). */
+hlf_status hlf_debug_bounds_probe(int64_t i, int64_t n, void* stream);
+
 /*
  * Stage 1, the CLA module (Section 2, steps (1)-(4); Fig. 1(b)).
  * A_dev:  [n][W] uint64, device, caller-owned; read until the factor kernel

@@ -169,6 +169,8 @@ __device__ void batch_store_chunk(const BatchArgs& a, int b, uint64_t first, uin
     }
     __syncthreads();
     uint64_t* out = a.out + a.out_off[b];
+    const long long room = (a.out_off[b + 1] - a.out_off[b]) / W;  // solutions the instance may store
+    (void)room;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint64_t g0 = first >> kStoreM, g1 = (first + len) >> kStoreM;
@@ -180,8 +182,8 @@ __device__ void batch_store_chunk(const BatchArgs& a, int b, uint64_t first, uin
         seed<W>(t, (h0 << kStoreM) + lane, z);
         for (uint64_t h = h0;;) {
             if constexpr (W == 1) {
-                st_cs(out + (h << kStoreM) + lane, z[0]);
-            } else {
+                if (HLF_IN_BOUNDS((h << kStoreM) + lane, room, kSiteBatchStore)) st_cs(out + (h << kStoreM) + lane, z[0]);
+            } else if (HLF_RANGE_IN_BOUNDS(h << kStoreM, 32, room, kSiteBatchStore)) {  // warp-uniform
                 store_warp_coalesced<W, false>(out + (h << kStoreM) * W, z, stage + warp * stage_words<W>(), lane);
             }
             if (++h == h1) break;
@@ -193,8 +195,10 @@ __device__ void batch_store_chunk(const BatchArgs& a, int b, uint64_t first, uin
         const uint64_t i = tail0 + threadIdx.x;
         uint64_t z[W];
         seed<W>(t, i, z);
+        if (HLF_IN_BOUNDS(i, room, kSiteBatchStore)) {
 #pragma unroll
-        for (int w = 0; w < W; ++w) out[i * W + w] = z[w];
+            for (int w = 0; w < W; ++w) out[i * W + w] = z[w];
+        }
     }
 }
 
@@ -334,6 +338,8 @@ hlf_status launch_batch(BatchArgs& a, int warps, int ctas_per_sm, cudaStream_t s
 }
 
 }  // namespace
+HLF_DEBUG_TAKE(batch)
+
 }  // namespace hlf
 
 // ---------------------------------------------------------------------------

@@ -195,10 +195,12 @@ __global__ void __launch_bounds__(kD1Threads, M == 64 ? 3 : 4) dense1_kernel(con
         if (Bulk && nw == (int)pass_words) {
             fence_smem_to_async_proxy();  // this lane's staged words, before the async proxy reads them
             __syncwarp();
-            if (lane == 0) bulk_store(out + w0, stage, (uint32_t)(pass_words * sizeof(uint64_t)));
+            if (lane == 0 && HLF_RANGE_IN_BOUNDS(w0, pass_words, pl.words, kSiteDenseStore))
+                bulk_store(out + w0, stage, (uint32_t)(pass_words * sizeof(uint64_t)));
         } else {
             __syncwarp();
-            for (int q = lane; q < nw; q += 32) st_cs(out + w0 + q, stage[q]);
+            for (int q = lane; q < nw; q += 32)
+                if (HLF_IN_BOUNDS(w0 + q, pl.words, kSiteDenseStore)) st_cs(out + w0 + q, stage[q]);
             __syncwarp();
         }
         if (++P == P1) break;
@@ -382,10 +384,12 @@ __global__ void __launch_bounds__(kD2Threads) dense2_kernel(const uint64_t* __re
         if (Bulk && nw == P * n) {
             fence_smem_to_async_proxy();
             __syncwarp();
-            if (lane == 0) bulk_store(out + w0, st, (uint32_t)(P * n * sizeof(uint64_t)));
+            if (lane == 0 && HLF_RANGE_IN_BOUNDS(w0, P * n, pl.words, kSiteDenseStore))
+                bulk_store(out + w0, st, (uint32_t)(P * n * sizeof(uint64_t)));
         } else {
             __syncwarp();
-            for (int q = lane; q < nw; q += 32) st_cs(out + w0 + q, st[q]);
+            for (int q = lane; q < nw; q += 32)
+                if (HLF_IN_BOUNDS(w0 + q, pl.words, kSiteDenseStore)) st_cs(out + w0 + q, st[q]);
             __syncwarp();
         }
         k += (uint64_t)pg;
@@ -653,14 +657,14 @@ __global__ void __launch_bounds__(kD3Threads, W == 3 ? 4 : (W == 4 ? 3 : (MW > 4
 #pragma unroll
             for (int m = 0; m < MW; ++m) {
                 const int q = lane + 32 * m;
-                if (q < K) st_cs(dst + q, G[m]);
+                if (q < K && HLF_IN_BOUNDS(kn - pl.a + q, pl.words, kSiteDenseStore)) st_cs(dst + q, G[m]);
             }
         } else {
 #pragma unroll
             for (int m = 0; m < MW; ++m) {
                 const int q = lane + 32 * m;
                 const uint64_t p = kn + q - pl.a;  // wraps to a huge value when negative
-                if (q < K && kn + q >= pl.a && p < pl.words)
+                if (q < K && kn + q >= pl.a && p < pl.words && HLF_IN_BOUNDS(p, pl.words, kSiteDenseStore))
                     st_cs(out + p, p == pl.words - 1 ? (G[m] & pl.last_mask) : G[m]);
             }
         }
@@ -778,5 +782,7 @@ hlf_status launch_store_dense(const uint64_t* table, int n, uint64_t offset, uin
     default: return HLF_ERR_SIZE;
     }
 }
+
+HLF_DEBUG_TAKE(dense)
 
 }  // namespace hlf

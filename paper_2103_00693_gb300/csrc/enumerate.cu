@@ -133,8 +133,10 @@ __global__ void __launch_bounds__(kThreads) store_kernel(const uint64_t* __restr
         const uint64_t i = gt < pl.n_head ? pl.offset + gt : pl.tail_first + (gt - pl.n_head);
         uint64_t z[W];
         seed<W>(t, i, z);
+        if (HLF_IN_BOUNDS(i - pl.offset, pl.count, kSiteStore)) {
 #pragma unroll
-        for (int w = 0; w < W; ++w) out[(i - pl.offset) * W + w] = z[w];
+            for (int w = 0; w < W; ++w) out[(i - pl.offset) * W + w] = z[w];
+        }
     }
 
     const uint64_t wg = gt >> 5;
@@ -151,15 +153,18 @@ __global__ void __launch_bounds__(kThreads) store_kernel(const uint64_t* __restr
         if constexpr (S == 2) {
             uint64_t* p = out + (h * G + (uint64_t)(S * lane) - pl.offset) * W;
             const uint64_t z1 = z[0] ^ t.B[0][0];  // g(2t+1) = g(2t) ^ 1
-            if (even) {
-                st_cs_v2(p, z[0], z1);
-            } else {
-                st_cs(p, z[0]);
-                st_cs(p + 1, z1);
+            if (HLF_RANGE_IN_BOUNDS(h * G + (uint64_t)(S * lane) - pl.offset, 2, pl.count, kSiteStore)) {
+                if (even) {
+                    st_cs_v2(p, z[0], z1);
+                } else {
+                    st_cs(p, z[0]);
+                    st_cs(p + 1, z1);
+                }
             }
-        } else {  // W > 1: out is 16-byte aligned (checked by the callers)
-            store_warp_coalesced<W, true>(out + (h * G - pl.offset) * W, z,
-                                          s_stage + (threadIdx.x >> 5) * stage_words<W>(), lane);
+        } else {  // W > 1: out is 16-byte aligned (checked by the callers); the check is warp-uniform
+            if (HLF_RANGE_IN_BOUNDS(h * G - pl.offset, G, pl.count, kSiteStore))
+                store_warp_coalesced<W, true>(out + (h * G - pl.offset) * W, z,
+                                              s_stage + (threadIdx.x >> 5) * stage_words<W>(), lane);
         }
         if (++h == h1) break;
         xor_row<W>(z, s_C[ctz64(h)]);
@@ -186,8 +191,10 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const uint64_t* __rest
         } else {
             seed<W>(t, i, z);
         }
+        if (HLF_IN_BOUNDS(j, m, kSiteStore)) {
 #pragma unroll
-        for (int w = 0; w < W; ++w) out[j * W + w] = z[w];
+            for (int w = 0; w < W; ++w) out[j * W + w] = z[w];
+        }
     }
 }
 
@@ -368,5 +375,7 @@ hlf_status launch_sample(const uint64_t* table, int W, int nb, const uint64_t* i
     HLF_DISPATCH_W(W, CALL)
 #undef CALL
 }
+
+HLF_DEBUG_TAKE(enumerate)
 
 }  // namespace hlf

@@ -266,8 +266,8 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
                 if (pk != kNone) {  // uniform
                     if (tid == 0) {
                         sm.colidx[b] = kp;
-                        sm.pivcol[rank + kp] = c0 + b;
-                        sm.rowpiv[pk >> 5] = (signed char)kp;
+                        if (HLF_IN_BOUNDS(rank + kp, HLF_MAX_N, kSiteFactorSmem)) sm.pivcol[rank + kp] = c0 + b;
+                        if (HLF_IN_BOUNDS(pk >> 5, HLF_MAX_N, kSiteFactorSmem)) sm.rowpiv[pk >> 5] = (signed char)kp;
                     }
                     ++kp;
                 }
@@ -278,7 +278,7 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
             for (int j = 0; j < R; ++j) {
                 if (key[j] == kNever) continue;
                 const int k = sm.rowpiv[tid + j * bs];
-                if (k < 0) continue;
+                if (k < 0 || !HLF_IN_BOUNDS(k, 32, kSiteFactorSmem)) continue;
                 sm.rowpiv[tid + j * bs] = -1;
                 my_kp[j] = k;
                 used[j] = true;
@@ -305,7 +305,7 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
                         if (((tx >> i) & 1) && k0 + i < kp) acc ^= sm.piv[k0 + i][w + v];
-                    sm.T2[tx * VP + v] = acc;
+                    if (HLF_IN_BOUNDS(tx * VP + v, 128 * (W | 1), kSiteFactorSmem)) sm.T2[tx * VP + v] = acc;
                 }
             }
             __syncthreads();
@@ -347,7 +347,7 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
     const int r = rank;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        if (!used[j]) continue;
+        if (!used[j] || !HLF_IN_BOUNDS(my_k[j], n, kSiteFactorSmem)) continue;
 #pragma unroll
         for (int v = 0; v < W; ++v) s_rows[my_k[j] * SW + v] = row[j][v];
     }
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(256) factor_kvec_kernel(const uint64_t* __rest
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if ((bk[u] >> fb) & 1ull)
+                if (((bk[u] >> fb) & 1ull) && HLF_IN_BOUNDS(pc[u] >> 6, W, kSiteFactorKvec))
                     atomicOr(reinterpret_cast<unsigned long long*>(&s_x[pc[u] >> 6]), 1ull << (pc[u] & 63));
         }
         __syncthreads();
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(256) factor_kvec_kernel(const uint64_t* __rest
         if (tid == 0) {
             const unsigned q = s_q & 3u;
             if (q & 1u) err = HLF_ERR_INTERNAL;  // q is even on Ker(A) for symmetric A
-            if (q >> 1) {
+            if ((q >> 1) && HLF_IN_BOUNDS(fw, W, kSiteFactorKvec)) {
                 atomicOr(reinterpret_cast<unsigned long long*>(o.table + kTableZ0Row * W + fw), 1ull << fb);
                 if (o.ptable)
                     atomicOr(reinterpret_cast<unsigned long long*>(o.ptable + kTableZ0Row * W + fw), 1ull << fb);
@@ -607,5 +607,7 @@ hlf_status launch_factor(const uint64_t* A, int n, int W, const FactorOut& o, cu
     default: return HLF_ERR_SIZE;
     }
 }
+
+HLF_DEBUG_TAKE(factor)
 
 }  // namespace hlf

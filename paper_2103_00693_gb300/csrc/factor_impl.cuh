@@ -210,7 +210,7 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
                         my_k[j] = rank;
                     }
                 }
-                if (tid == 0) sm.pivcol[rank] = c;
+                if (tid == 0 && HLF_IN_BOUNDS(rank, HLF_MAX_N, kSiteFactorSmem)) sm.pivcol[rank] = c;
                 if constexpr (R == 1) {  // row p; its words below word w are zero
                     uint64_t pv[W];
 #pragma unroll
@@ -233,7 +233,7 @@ __device__ int factor_block(const uint64_t* __restrict__ A, int n, const FactorO
         r = rank;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            if (!used[j]) continue;
+            if (!used[j] || !HLF_IN_BOUNDS(my_k[j], n, kSiteFactorSmem)) continue;
 #pragma unroll
             for (int v = 0; v < W; ++v) s_rows[my_k[j] * SW + v] = row[j][v];
         }

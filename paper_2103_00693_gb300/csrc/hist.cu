@@ -76,7 +76,11 @@ __device__ __forceinline__ uint32_t seed_field(const FieldTable& t, uint64_t i)
 // Bins in shared memory: v is the byte offset of the counter.
 struct SmemSink {
     unsigned char* base;
-    __device__ __forceinline__ void consume(uint32_t v) { atomicAdd(reinterpret_cast<uint32_t*>(base + v), 1u); }
+    uint32_t nb;  // bins
+    __device__ __forceinline__ void consume(uint32_t v)
+    {
+        if (HLF_IN_BOUNDS(v >> 2, nb, kSiteHistBin)) atomicAdd(reinterpret_cast<uint32_t*>(base + v), 1u);
+    }
     __device__ __forceinline__ void flush() {}
 };
 
@@ -87,6 +91,7 @@ struct SmemSink {
 template <bool Coalesce>
 struct GlobalSink {
     unsigned long long* bins;
+    uint32_t nb;  // bins
     uint32_t cur = 0;
     uint32_t pending = 0;
     __device__ __forceinline__ void consume(uint32_t v)
@@ -95,17 +100,18 @@ struct GlobalSink {
             if (v == cur) {
                 ++pending;
             } else {
-                if (pending) atomicAdd(&bins[cur], (unsigned long long)pending);
+                if (pending && HLF_IN_BOUNDS(cur, nb, kSiteHistBin)) atomicAdd(&bins[cur], (unsigned long long)pending);
                 cur = v;
                 pending = 1;
             }
         } else {
-            atomicAdd(&bins[v], 1ull);
+            if (HLF_IN_BOUNDS(v, nb, kSiteHistBin)) atomicAdd(&bins[v], 1ull);
         }
     }
     __device__ __forceinline__ void flush()
     {
-        if (Coalesce && pending) atomicAdd(&bins[cur], (unsigned long long)pending);
+        if (Coalesce && pending && HLF_IN_BOUNDS(cur, nb, kSiteHistBin))
+            atomicAdd(&bins[cur], (unsigned long long)pending);
         pending = 0;
     }
 };
@@ -187,6 +193,7 @@ __global__ void __launch_bounds__(kThreads) hist_interleaved_kernel(const uint64
     Sink sink;
     if constexpr (InSmem) sink.base = reinterpret_cast<unsigned char*>(s_bins);
     else sink.bins = out;
+    sink.nb = nb;
     const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gt < pl.n_head + pl.n_tail) {  // ragged head and tail, one index per thread
         const uint64_t i = gt < pl.n_head ? pl.offset + gt : pl.tail_first + (gt - pl.n_head);
@@ -247,6 +254,7 @@ __global__ void __launch_bounds__(kThreads) hist_runs_kernel(const uint64_t* __r
     Sink sink;
     if constexpr (InSmem) sink.base = reinterpret_cast<unsigned char*>(s_bins);
     else sink.bins = out;
+    sink.nb = nb;
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g < pl.used) {
         uint64_t i = pl.offset + g * pl.per_thread;
@@ -388,5 +396,7 @@ hlf_status launch_histogram(const uint64_t* table, int W, uint64_t offset, uint6
     if (nbits <= kHistSmemBits) return launch_hist_k<true>(table, W, offset, count, lo, nbits, out, s);
     return launch_hist_k<false>(table, W, offset, count, lo, nbits, out, s);
 }
+
+HLF_DEBUG_TAKE(hist)
 
 }  // namespace hlf

@@ -270,6 +270,18 @@ bool take_injected_alloc_failure()
     return false;
 }
 
+HLF_DEBUG_TAKE(api)
+
+namespace {
+
+// one thread, no memory access: the check itself (site kSiteProbe)
+__global__ void debug_probe_kernel(long long i, long long n)
+{
+    (void)HLF_IN_BOUNDS(i, n, kSiteProbe);
+}
+
+}  // namespace
+
 int sm_count()
 {
     static int cache[64] = {0};
@@ -308,6 +320,30 @@ hlf_status hlf_debug_fail_allocs(int32_t count)
     if (count < 0) return HLF_ERR_ARG;
     hlf::g_fail_allocs.store(count, std::memory_order_relaxed);
     return HLF_OK;
+}
+
+hlf_status hlf_debug_violation(uint64_t* first, int32_t* is_debug)
+{
+    if (!first || !is_debug) return HLF_ERR_ARG;
+    *is_debug = hlf::kDebugBuild ? 1 : 0;
+    *first = 0;
+    if (!hlf::kDebugBuild) return HLF_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return HLF_ERR_CUDA;
+    uint64_t (*const take[])() = {hlf::debug_take_api,  hlf::debug_take_enumerate, hlf::debug_take_many,
+                                   hlf::debug_take_upto, hlf::debug_take_batch,     hlf::debug_take_dense,
+                                   hlf::debug_take_factor, hlf::debug_take_hist};
+    for (auto f : take) {  // every word is read (and so cleared); the first record is kept
+        const uint64_t v = f();
+        if (v == ~0ull) return HLF_ERR_CUDA;
+        if (v && !*first) *first = v;
+    }
+    return HLF_OK;
+}
+
+hlf_status hlf_debug_bounds_probe(int64_t i, int64_t n, void* stream)
+{
+    hlf::debug_probe_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(i, n);
+    return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
 int32_t hlf_device_count(void)

@@ -33,6 +33,66 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// ---------------------------------------------------------------- debug build
+// Bounds checks of the debug build (compiled with -DHLF_DEBUG, the library
+// the binding loads when HLF_DEBUG=1): a failed check skips the access it
+// guards and records the first failure, 2^63 | (site << 48) | (index mod
+// 2^48), in a device word of its translation unit; hlf_debug_violation reads
+// and clears the words of all of them. Release builds compile every check to
+// `true`. The sites:
+enum DebugSite : int {
+    kSiteProbe = 1,      // hlf_debug_bounds_probe
+    kSiteStore = 2,      // store_kernel, sample_kernel: solution words vs count * W
+    kSiteManyStore = 3,  // many_kernel: solution words vs the window's count * W
+    kSiteUptoStore = 4,  // store_upto_kernel: solution words vs cap * W
+    kSiteBatchStore = 5, // batch_kernel store items: words vs the instance's output
+    kSiteDenseStore = 6, // dense kernels: stream words vs the stream's length
+    kSiteFactorSmem = 7, // factor: panel tables, pivot lists, basis rows
+    kSiteFactorKvec = 8, // factor_kvec_kernel: mask words, x_f words, table words
+    kSiteHistBin = 9,    // histogram kernels: bins vs the bin count
+};
+
+#ifdef HLF_DEBUG
+static __device__ unsigned long long g_hlf_violation;  // one per translation unit
+
+__device__ __forceinline__ bool debug_in_bounds(long long i, long long n, int site)
+{
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&g_hlf_violation, 0ull,
+              (1ull << 63) | ((unsigned long long)site << 48) | ((unsigned long long)i & ((1ull << 48) - 1)));
+    return false;
+}
+#define HLF_IN_BOUNDS(i, n, site) ::hlf::debug_in_bounds((long long)(i), (long long)(n), (site))
+// [i, i + len) inside [0, n)
+#define HLF_RANGE_IN_BOUNDS(i, len, n, site) \
+    (HLF_IN_BOUNDS((i), (n), (site)) && HLF_IN_BOUNDS((long long)(i) + (long long)(len) - 1, (n), (site)))
+// the host side of a translation unit's word: read it and clear it
+#define HLF_DEBUG_TAKE(name)                                                                   \
+    uint64_t debug_take_##name()                                                               \
+    {                                                                                          \
+        unsigned long long v = 0, z = 0;                                                       \
+        if (cudaMemcpyFromSymbol(&v, g_hlf_violation, sizeof v) != cudaSuccess) return ~0ull;  \
+        cudaMemcpyToSymbol(g_hlf_violation, &z, sizeof z);                                     \
+        return v;                                                                              \
+    }
+constexpr bool kDebugBuild = true;
+#else
+#define HLF_IN_BOUNDS(i, n, site) true
+#define HLF_RANGE_IN_BOUNDS(i, len, n, site) true
+#define HLF_DEBUG_TAKE(name) \
+    uint64_t debug_take_##name() { return 0; }
+constexpr bool kDebugBuild = false;
+#endif
+// one per translation unit with checks (defined there by HLF_DEBUG_TAKE)
+uint64_t debug_take_api();
+uint64_t debug_take_enumerate();
+uint64_t debug_take_many();
+uint64_t debug_take_upto();
+uint64_t debug_take_batch();
+uint64_t debug_take_dense();
+uint64_t debug_take_factor();
+uint64_t debug_take_hist();
+
 constexpr int kTableRows = 65;      // B_0..B_64 (row 64 always zero)
 constexpr int kTableZ0Row = 65;     // z0 follows the basis rows
 constexpr int kTableTotalRows = 66;

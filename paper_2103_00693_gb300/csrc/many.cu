@@ -59,8 +59,10 @@ __device__ void many_task(const WinDesc& d, uint64_t u, int lane, uint64_t* stag
             const uint64_t i = e < d.n_head ? d.offset + e : d.tail_first + (e - d.n_head);
             uint64_t z[W];
             seed_g<W>(d.table, i, z);
+            if (HLF_IN_BOUNDS(i - d.offset, d.count, kSiteManyStore)) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) d.out[(i - d.offset) * W + w] = z[w];
+                for (int w = 0; w < W; ++w) d.out[(i - d.offset) * W + w] = z[w];
+            }
         }
         return;
     }
@@ -75,14 +77,17 @@ __device__ void many_task(const WinDesc& d, uint64_t u, int lane, uint64_t* stag
         if constexpr (S == 2) {
             uint64_t* p = d.out + (h * G + (uint64_t)(S * lane) - d.offset) * W;
             const uint64_t z1 = z[0] ^ __ldg(d.table);  // g(2t+1) = g(2t) ^ 1
-            if (even) {
-                st_cs_v2(p, z[0], z1);
-            } else {
-                st_cs(p, z[0]);
-                st_cs(p + 1, z1);
+            if (HLF_RANGE_IN_BOUNDS(h * G + (uint64_t)(S * lane) - d.offset, 2, d.count, kSiteManyStore)) {
+                if (even) {
+                    st_cs_v2(p, z[0], z1);
+                } else {
+                    st_cs(p, z[0]);
+                    st_cs(p + 1, z1);
+                }
             }
-        } else {
-            store_warp_coalesced<W, true>(d.out + (h * G - d.offset) * W, z, stage, lane);
+        } else {  // the check is warp-uniform
+            if (HLF_RANGE_IN_BOUNDS(h * G - d.offset, G, d.count, kSiteManyStore))
+                store_warp_coalesced<W, true>(d.out + (h * G - d.offset) * W, z, stage, lane);
         }
         if (++h == h1) break;
         const int j = ctz64(h);
@@ -162,6 +167,8 @@ void plan_window(WinDesc& d, uint32_t W)
 // use of the handle on a stream (defined in hlf_api.cu).
 hlf_status handle_enum_view(hlf_handle* h, const uint64_t** table, int32_t* r, int32_t* W);
 hlf_status handle_record_use(hlf_handle* h, cudaStream_t s);
+
+HLF_DEBUG_TAKE(many)
 
 }  // namespace hlf
 

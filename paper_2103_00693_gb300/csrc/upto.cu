@@ -34,8 +34,10 @@ __global__ void __launch_bounds__(kThreads) store_upto_kernel(const uint64_t* __
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t z[W];
         seed<W>(t, i, z);
+        if (HLF_IN_BOUNDS(i, cap, kSiteUptoStore)) {
 #pragma unroll
-        for (int w = 0; w < W; ++w) out[i * W + w] = z[w];
+            for (int w = 0; w < W; ++w) out[i * W + w] = z[w];
+        }
     }
 }
 
@@ -154,5 +156,7 @@ hlf_status launch_store_upto(const uint64_t* table, int W, const int32_t* info, 
     default: return HLF_ERR_SIZE;
     }
 }
+
+HLF_DEBUG_TAKE(upto)
 
 }  // namespace hlf

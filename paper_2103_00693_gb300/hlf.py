@@ -41,6 +41,8 @@ SIGNATURES = {
     "hlf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hlf_device_count": (_i32, []),
     "hlf_debug_fail_allocs": (ctypes.c_int, [_i32]),
+    "hlf_debug_violation": (ctypes.c_int, [ctypes.POINTER(_u64), ctypes.POINTER(_i32)]),
+    "hlf_debug_bounds_probe": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _vp]),
     "hlf_factor": (ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(_vp)]),
     "hlf_get_rank": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "hlf_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -82,20 +84,27 @@ class HlfError(RuntimeError):
 _LIB = None
 
 
+def debug_requested() -> bool:
+    """HLF_DEBUG=1 selects the debug library (bounds-checked kernels)."""
+    return os.environ.get("HLF_DEBUG", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_requested() else _build.LIB
 
 
 def load(build_if_missing: bool = False):
-    """Load libhlf.so. Raises if it is missing (unless build_if_missing)."""
+    """Load libhlf.so (libhlf_debug.so under HLF_DEBUG=1). Raises if it is
+    missing (unless build_if_missing)."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    if not os.path.exists(_build.LIB):
+    path = lib_path()
+    if not os.path.exists(path):
         if not build_if_missing:
-            raise RuntimeError(f"libhlf.so is not built ({_build.LIB}); run __graft_entry__.build()")
-        _build.build()
-    lib = ctypes.CDLL(_build.LIB)
+            raise RuntimeError(f"{os.path.basename(path)} is not built ({path}); run __graft_entry__.build()")
+        _build.build(debug=debug_requested())
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res
@@ -178,6 +187,21 @@ def hlf_debug_fail_allocs(count: int):
     """Fault injection for tests: the next `count` allocating calls fail with
     HLF_ERR_NOMEM (host-side; no GPU involved)."""
     _check(load().hlf_debug_fail_allocs(count), "hlf_debug_fail_allocs")
+
+
+def hlf_debug_violation() -> tuple[int, bool]:
+    """(the first failed bounds check recorded since the last call, 0 if none,
+    2^63 | site << 48 | index mod 2^48; whether the loaded library is the
+    debug build). Synchronises the device and clears the record."""
+    first, dbg = _u64(0), _i32(0)
+    _check(load().hlf_debug_violation(ctypes.byref(first), ctypes.byref(dbg)), "hlf_debug_violation")
+    return int(first.value), bool(dbg.value)
+
+
+def hlf_debug_bounds_probe(i: int, n: int, stream=None):
+    """One device thread checks index i against [0, n) (site 1), touching no
+    memory: a failed check is recorded in the debug build."""
+    _check(load().hlf_debug_bounds_probe(i, n, _stream_ptr(stream)), "hlf_debug_bounds_probe")
 
 
 def hlf_factor(A_dev, n: int, stream=None) -> int:

@@ -46,3 +46,17 @@ def cuda_ok():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return True
+
+
+@pytest.fixture(autouse=True)
+def _debug_build_bounds(request):
+    """Under HLF_DEBUG=1 (the bounds-checked debug library) a GPU test also
+    fails if a kernel it ran recorded a failed bounds check."""
+    yield
+    if os.environ.get("HLF_DEBUG") != "1" or request.node.get_closest_marker("gpu") is None:
+        return
+    from paper_2103_00693_gb300 import hlf
+
+    first, is_debug = hlf.hlf_debug_violation()
+    assert is_debug, "HLF_DEBUG=1 but the loaded library is the release build"
+    assert first == 0, f"failed bounds check: site {(first >> 48) & 0x7fff}, index {first & ((1 << 48) - 1)}"

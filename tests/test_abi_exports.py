@@ -116,6 +116,16 @@ def test_injected_allocation_failures_are_nomem(lib):
     assert lib.hlf_debug_fail_allocs(0) == 0
 
 
+def test_release_library_is_not_the_debug_build(lib):
+    """The release library reports that it is not the debug build and that
+    no check failed, without touching a GPU; null pointers are HLF_ERR_ARG."""
+    first, dbg = ctypes.c_uint64(7), ctypes.c_int32(7)
+    assert lib.hlf_debug_violation(ctypes.byref(first), ctypes.byref(dbg)) == 0
+    assert (first.value, dbg.value) == (0, 0)
+    assert lib.hlf_debug_violation(None, ctypes.byref(dbg)) == 1
+    assert lib.hlf_debug_violation(ctypes.byref(first), None) == 1
+
+
 def test_package_reexports_every_entry_point():
     """Every C entry point has a same-named function in the package (the
     status-string and device-count helpers included)."""

@@ -10,9 +10,24 @@ the library's batch kernel.
 
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from . import hlf
+
+
+def spin_limit_from_env() -> int | None:
+    """HLF_SPIN_LIMIT: the bound on a chunk's polls for its matrix (see
+    hlf_batch_set_spin_limit), for every plan this module creates; unset
+    keeps the library's default."""
+    v = os.environ.get("HLF_SPIN_LIMIT", "")
+    if not v:
+        return None
+    limit = int(v, 0)
+    if not 1 <= limit < 1 << 32:
+        raise ValueError("HLF_SPIN_LIMIT must be in [1, 2^32)")
+    return limit
 
 
 class Batch:
@@ -39,6 +54,9 @@ class Batch:
         self.plan = hlf.hlf_batch_create(max(self.count, 1))
         self.tiles = (8, 0, 1 << 16)
         self.graph = None
+        limit = spin_limit_from_env()
+        if limit is not None:
+            hlf.hlf_batch_set_spin_limit(self.plan, limit)
 
     def set_tiles(self, warps_per_item: int, ctas_per_sm: int, chunk: int):
         hlf.hlf_batch_set_tiles(self.plan, warps_per_item, ctas_per_sm, chunk)

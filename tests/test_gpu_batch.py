@@ -103,6 +103,17 @@ def test_batch_graph_replay(cuda_ok):
     B.close()
 
 
+def test_spin_limit_from_the_environment(cuda_ok, monkeypatch):
+    """HLF_SPIN_LIMIT sets the bound of every plan the module creates: with
+    200 polls and the factor items skipped, the waits run out at once."""
+    monkeypatch.setenv("HLF_SPIN_LIMIT", "200")
+    B = Batch(synth.batch_instances(4, 4, 6, 0.5, 12))
+    hlf.hlf_batch_set_debug(B.plan, 1)
+    B.run(1 << 12)
+    assert B.status() == hlf.STATUS_CODES["HLF_ERR_TIMEOUT"]
+    B.close()
+
+
 def test_batch_timeout_reports_and_recovers(cuda_ok):
     """Every chunk waits on a flag that nothing sets (the factor items are
     skipped); the bounded waits run out, the status says so, and the next

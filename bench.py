@@ -160,6 +160,13 @@ class ClockSampler:
                  "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi's start-up (NVML initialisation) can stall the host's
+        # launches and waits for tens of ms: let it write its first sample
+        # before the caller opens the timed region (bounded wait)
+        t_end = time.time() + 3.0
+        while time.time() < t_end and self.proc.poll() is None and os.path.getsize(self.file.name) == 0:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -380,9 +387,9 @@ def run_hlf(args, world, rank, local):
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
+    clocks.start()
     barrier(world)
     torch.cuda.synchronize(dev)
-    clocks.start()
     start.record(stream)
     for k in range(args.steps):
         step(evs[k])

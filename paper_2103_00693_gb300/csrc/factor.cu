@@ -1,10 +1,10 @@
 // Stage 1 for one matrix (the CLA module of Section 2, steps (1)-(4)).
 //
-// n <= 512 (W <= 8): one CTA runs factor_block (factor_impl.cuh): input
+// n <= 384 (W <= 6): one CTA runs factor_block (factor_impl.cuh): input
 // checks, elimination, kernel vectors, q and z^a in one launch, which is what
 // the latency of small and medium instances wants.
 //
-// n > 512 (W >= 9): the same results from two launches that spread the work
+// n > 384 (W >= 7): the same results from two launches that spread the work
 // that does not have to be sequential over many SMs:
 //   factor_elim_kernel   CTA 0 runs the Gauss-Jordan elimination (step (1))
 //                        with the rows of A in registers, in panels of 32
@@ -16,10 +16,11 @@
 //                        kernel vector x_f, q(x_f) mod 4 and the bit z^a_f
 //                        (steps (2)-(4)), the paper-order table, and, in
 //                        the last CTA to finish, the status and rank.
-// At n = 1024 (grid 32 x 32) this takes 334 us; one CTA running
-// factor_block's column loop for everything took 392 us. At n = 484 the
-// second launch costs more than it saves (143 us against 124 us), hence the
-// threshold.
+// At n = 1024 (grid 32 x 32) this takes 304 us; one CTA running
+// factor_block's column loop for everything took 392 us. Against the one-CTA
+// path it saves 4-12% from W = 7 on (n = 400: 99 us against 105; n = 512:
+// 123 us against 140), ties at W = 6 and loses at W = 5 (n = 289: 70 us
+// against 67), hence the threshold.
 //
 // Where the elimination's time goes at n = 1024 (random symmetric, full
 // rank; clock64 phase counters, 667k cycles): the pivot search 365k (356
@@ -77,7 +78,7 @@ hlf_status launch_factor_w(const uint64_t* A, int n, const FactorOut& o, cudaStr
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
-// ------------------------------------------------------------ n > 512
+// ------------------------------------------------------------ n > 384
 
 constexpr int kChkCtas = 8;       // CTAs that check the input beside the elimination
 constexpr int kWorkR = 16;        // work[16] = r
@@ -594,8 +595,8 @@ hlf_status launch_factor(const uint64_t* A, int n, int W, const FactorOut& o, cu
     case 4: return launch_factor_w<4>(A, n, o, s);
     case 5: return launch_factor_w<5>(A, n, o, s);
     case 6: return launch_factor_w<6>(A, n, o, s);
-    case 7: return launch_factor_w<7>(A, n, o, s);
-    case 8: return launch_factor_w<8>(A, n, o, s);
+    case 7: return launch_factor_large<7>(A, n, o, s);
+    case 8: return launch_factor_large<8>(A, n, o, s);
     case 9: return launch_factor_large<9>(A, n, o, s);
     case 10: return launch_factor_large<10>(A, n, o, s);
     case 11: return launch_factor_large<11>(A, n, o, s);

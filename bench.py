@@ -71,9 +71,9 @@ KERNEL_SOURCES = {
     "dense1_kernel<16,1,1>": ["dense.cu", "enum_impl.cuh", "hlf_internal.cuh"],
 }
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
-    "reduce_kernel<1,6,1024>": {"bytes": 743168 + 0, "sources": "1de446fddcf41e74"},
-    "store_kernel<1,2>": {"bytes": 701952 + 8525239808, "sources": "1de446fddcf41e74"},
-    "dense1_kernel<16,1,1>": {"bytes": 85504 + 4767099648, "sources": "b226170a230afc66"},
+    "reduce_kernel<1,6,1024>": {"bytes": 541440 + 1536, "sources": "0b975b98a6be7595"},
+    "store_kernel<1,2>": {"bytes": 244992 + 8525198848, "sources": "0b975b98a6be7595"},
+    "dense1_kernel<16,1,1>": {"bytes": 630528 + 4767081216, "sources": "5acb1cca73b98019"},
 }
 
 

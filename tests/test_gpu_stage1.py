@@ -40,6 +40,20 @@ def _cases():
         c.append((f"lowrank{n}-{k}", ((X @ X.T) & 1).astype(np.uint8)))
     c.append(("sparse300", synth.random_symmetric(300, 0.01, 3)))
     c.append(("dense1000", synth.random_symmetric(1000, 0.9, 4)))
+    # the panel path's lower end (W = 7, 8: n = 385..512) and its boundary
+    for N in (20, 22):
+        c.append((f"grid{N}-p.5", synth.grid_instance(N, 0.5, 30 + N)))
+        c.append((f"grid{N}-full", synth.grid_instance(N, 1.0, 40 + N)))
+    for n in (384, 385, 448, 449):
+        c.append((f"sym{n}", synth.random_symmetric(n, 0.5, n)))
+    A = synth.random_symmetric(500, 0.5, 77)
+    A[:400, :] = 0
+    A[:, :400] = 0
+    c.append(("late500-400", A))
+    X = np.random.default_rng(8).integers(0, 2, size=(450, 12), dtype=np.int64)
+    c.append(("lowrank450-12", ((X @ X.T) & 1).astype(np.uint8)))
+    c.append(("zero400", np.zeros((400, 400), dtype=np.uint8)))
+    c.append(("eye450", np.eye(450, dtype=np.uint8)))
     return c
 
 

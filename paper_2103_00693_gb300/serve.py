@@ -22,8 +22,9 @@ Continuous batching (Server.run):
     factorisation stays resident (one handle) meanwhile;
   * every tick, all factored windows that got their memory are
     materialised by ONE hlf_enumerate_store_many launch on the enumeration
-    stream, into the staging ring, while earlier ticks' windows are still
-    being copied out and later requests are being factored;
+    stream (hlf_enumerate_store when the tick has one window), into the
+    staging ring, while earlier ticks' windows are still being copied out
+    and later requests are being factored;
   * each window is copied to its slot of a pinned host ring on a copy stream;
     a request completes when its copy event has fired
     (latency = completion - arrival).
@@ -192,6 +193,24 @@ class Stats:
                 "busy_frac": self.busy_s / self.makespan_s if self.makespan_s else 0.0,
                 "ticks": self.ticks, "launches": self.launches,
                 "failed": self.failed, "cancelled": self.cancelled, "refused": self.refused}
+
+
+_SPIN_S = 150e-6  # the last stretch before a known arrival is spun, not slept
+
+
+def _wait_until(t0: float, t: float, cap_s: float = float("inf")):
+    """Wait until perf_counter() - t0 >= t, or return after cap_s when t is
+    further away: sleep to within _SPIN_S of t, spin the rest. A sleep wakes
+    tens of microseconds late, which would add to the latency of the request
+    arriving at t. Both the served and the plain loop wait this way."""
+    dt = t - (time.perf_counter() - t0)
+    if dt > cap_s + _SPIN_S:  # not due yet: one sleep, the caller comes back
+        time.sleep(cap_s)
+        return
+    if dt > _SPIN_S:
+        time.sleep(dt - _SPIN_S)
+    while time.perf_counter() - t0 < t:
+        pass
 
 
 @contextlib.contextmanager
@@ -485,9 +504,14 @@ class Server:
             if ready:
                 torch.cuda.nvtx.range_push("serve.tick")  # one window launch and its copies
                 try:
-                    hlf.hlf_enumerate_store_many(
-                        self.many, [q.h for q in ready], [q.offset for q in ready], [q.count for q in ready],
-                        [self.dev_ring.view(q.blk_dev, q.count * q.W) for q in ready], self.s_enum)
+                    if len(ready) == 1:  # one window: the single-window call marshals less
+                        q = ready[0]
+                        hlf.hlf_enumerate_store(q.h, q.offset, q.count, self.dev_ring.view(q.blk_dev, q.count * q.W),
+                                                self.s_enum)
+                    else:
+                        hlf.hlf_enumerate_store_many(
+                            self.many, [q.h for q in ready], [q.offset for q in ready], [q.count for q in ready],
+                            [self.dev_ring.view(q.blk_dev, q.count * q.W) for q in ready], self.s_enum)
                 except hlf.HlfError as e:
                     t = time.perf_counter() - t0
                     for q in ready:
@@ -530,10 +554,23 @@ class Server:
                 if waiting and not any(factoring) and not pending and not copying:
                     dt = waiting[0].t_arrival - (time.perf_counter() - t0)
                     if dt > 0:
-                        time.sleep(min(dt, 0.001))
-                # with work in flight the loop polls its events without
-                # sleeping: a sleep of a few microseconds lasts ~60 us on
-                # Linux, which would add to every request's latency
+                        _wait_until(t0, waiting[0].t_arrival, 0.001)
+                elif not pending:
+                    # only events to wait for: poll just those until one
+                    # fires, the next request or timed cancellation is due,
+                    # or a cancel() comes in; a whole pass of the loop per
+                    # poll would add its cost to the request's latency. (With
+                    # work in flight the loop never sleeps: a sleep of a few
+                    # microseconds lasts ~60 us on Linux.)
+                    evs = [fq[0].ev_factor for fq in factoring if fq]
+                    if copying:
+                        evs.append(copying[0].ev_copy)
+                    t_next = waiting[0].t_arrival if waiting else float("inf")
+                    if next_cancel < len(cancels):
+                        t_next = min(t_next, cancels[next_cancel][0])
+                    while (not self._cancel and time.perf_counter() - t0 < t_next
+                           and not any(e.query() for e in evs)):
+                        pass
         st.makespan_s = time.perf_counter() - t0
         if busy_since is not None:
             st.busy_s += st.makespan_s - busy_since
@@ -574,7 +611,7 @@ def _run_plain(stream, keep_results, host_bytes, device_bytes):
     for q in reqs:
         now = time.perf_counter() - t0
         if q.t_arrival > now:
-            time.sleep(q.t_arrival - now)
+            _wait_until(t0, q.t_arrival)
         t_start = time.perf_counter() - t0
         if q.t_cancel is not None and q.t_cancel <= t_start:
             end(q, CANCELLED, 0)

@@ -39,6 +39,9 @@
 //   - two columns per barrier (each warp offering its lowest rows with bit
 //     0, with bit 1 and with bit 0 xor bit 1 set, which settles the pivots
 //     of both columns): 345 us, the search 405 cycles a column;
+//   - the search in one warp with the rows transposed (lane l holding rows
+//     32l..32l+31 as column words): no CTA barrier, but 611 cycles a column,
+//     the pivot slice's extraction being a chain of dependent ORs (370 us);
 //   - a thread-block cluster sharing the rows: its barrier alone takes about
 //     400 cycles a round trip on this GPU (any cluster size), and a
 //     publish-then-minimum exchange over 8 CTAs about 800, more than the

@@ -119,6 +119,24 @@ def ops_per_solution(W: int) -> int:
     return OPS_PER_SOLUTION_W1 + 22 * (W - 1)
 
 
+def alu_pipe_ops_per_solution(W: int) -> int:
+    """Of those, the ones only the ALU pipe executes: 12 at W = 1, and per
+    further word its step XOR 2, the XOR into the running hash 2 and the
+    three xor-shifts of its SplitMix64 round 12 (the round's two multiplies
+    run on the FMA pipe)."""
+    return ALU_PIPE_OPS_PER_SOLUTION_W1 + 16 * (W - 1)
+
+
+def alu_pipe_peak(dev=None):
+    """(peak ALU-pipe ops/s in T, its basis): 64 lanes per clock per SM."""
+    import torch
+
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device() if dev is None else dev).multi_processor_count
+    peak = sms * ALU_PIPE_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 / 1e12
+    return peak, f"{sms} SMs x {ALU_PIPE_LANES_PER_SM_CLK} ALU-pipe lanes/clk x {pk['sm_max_mhz']:.0f} MHz"
+
+
 def int_peak(dev=None):
     """(peak 32-bit integer ops/s in T, its basis): every SM's four
     schedulers issuing one 32-lane instruction per clock at the maximum SM
@@ -685,11 +703,13 @@ def run_configs(dev):
     return out
 
 
-def batched_ops(Ws, counts) -> int:
+def batched_ops(Ws, counts, per_solution=None) -> int:
     """Algorithmic 32-bit integer operations of the batched reduce: the
     single-instance reduce's 22W - 4 per solution (18 at W = 1), summed over
-    the instances' solution counts; factorisation work is not counted."""
-    return int(sum(int(c) * ops_per_solution(int(w)) for w, c in zip(Ws, counts)))
+    the instances' solution counts; factorisation work is not counted.
+    per_solution picks another count (the ALU-pipe one)."""
+    f = per_solution or ops_per_solution
+    return int(sum(int(c) * f(int(w)) for w, c in zip(Ws, counts)))
 
 
 def run_batched(args):
@@ -728,6 +748,8 @@ def run_batched(args):
     sols = sum(counts)
     ops = batched_ops(B.Ws, counts)
     ipk, ipk_basis = int_peak()
+    alu_ops = batched_ops(B.Ws, counts, alu_pipe_ops_per_solution)
+    apk, apk_basis = alu_pipe_peak()
     # the two-call form of the same work
     for _ in range(2):
         B.factor()
@@ -775,6 +797,10 @@ def run_batched(args):
                          "unit": "Tops/s", "frac": ops / (ms / 1e3) / 1e12 / ipk,
                          "ops_per_batch": ops, "ops_per_solution": "22W - 4 (18 at W = 1)",
                          "kernel": "batch_kernel", "peak_basis": ipk_basis},
+            "roofline_alu_pipe": {"bound": "alu_pipe", "achieved": alu_ops / (ms / 1e3) / 1e12, "peak": apk,
+                                  "unit": "Tops/s", "frac": alu_ops / (ms / 1e3) / 1e12 / apk,
+                                  "ops_per_batch": alu_ops, "ops_per_solution": "16W - 4 (12 at W = 1)",
+                                  "kernel": "batch_kernel", "peak_basis": apk_basis + " (the pipe that binds)"},
             "split_calls_ms_per_batch": split_ms,
             "store": {"what": "hlf_enumerate_batched storing min(2^r, 2^14) solutions of every grid",
                       "ms": store_ms, "bytes": store_bytes,

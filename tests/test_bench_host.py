@@ -32,3 +32,13 @@ def test_traffic_is_null_once_the_sources_change(monkeypatch):
         assert b.traffic(k) is None
         monkeypatch.undo()
     assert b.traffic("no_such_kernel") is None
+
+
+def test_operation_counts():
+    """The reduce's op count per solution and its ALU-pipe part: 18 and 12 at
+    W = 1; every word beyond the first adds 22, of which 16 on the ALU pipe
+    (the other 6 are its round's two 64-bit multiplies, 3 IMAD each)."""
+    assert bench.ops_per_solution(1) == 18 and bench.alu_pipe_ops_per_solution(1) == 12
+    for W in range(1, 17):
+        assert bench.ops_per_solution(W) - bench.alu_pipe_ops_per_solution(W) == 6 * W
+    assert bench.batched_ops([1, 2], [10, 10], bench.alu_pipe_ops_per_solution) == 10 * 12 + 10 * 28

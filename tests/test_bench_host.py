@@ -38,7 +38,8 @@ def test_operation_counts():
     """The reduce's op count per solution and its ALU-pipe part: 18 and 12 at
     W = 1; every word beyond the first adds 22, of which 16 on the ALU pipe
     (the other 6 are its round's two 64-bit multiplies, 3 IMAD each)."""
-    assert bench.ops_per_solution(1) == 18 and bench.alu_pipe_ops_per_solution(1) == 12
+    b = _bench()
+    assert b.ops_per_solution(1) == 18 and b.alu_pipe_ops_per_solution(1) == 12
     for W in range(1, 17):
-        assert bench.ops_per_solution(W) - bench.alu_pipe_ops_per_solution(W) == 6 * W
-    assert bench.batched_ops([1, 2], [10, 10], bench.alu_pipe_ops_per_solution) == 10 * 12 + 10 * 28
+        assert b.ops_per_solution(W) - b.alu_pipe_ops_per_solution(W) == 6 * W
+    assert b.batched_ops([1, 2], [10, 10], b.alu_pipe_ops_per_solution) == 10 * 12 + 10 * 28

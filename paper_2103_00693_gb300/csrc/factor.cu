@@ -144,7 +144,7 @@ __device__ __noinline__ void invert_panel(int kp, const uint32_t* st_piv, const 
     if (ci >= 0) H[ci] = hv;
 }
 
-template <int W, int NW>
+template <int W>
 struct ElimSmem {
     int first[2][32];          // per warp: its lowest candidate's key, by column parity
     uint32_t cw[2][32];        // and that row's current slice
@@ -159,10 +159,10 @@ struct ElimSmem {
     int pivcol[HLF_MAX_N];
 };
 
-template <int W, int NW>
+template <int W>
 constexpr size_t elim_smem_bytes(int n)
 {
-    return sizeof(ElimSmem<W, NW>) + (size_t)n * basis_stride<W>() * sizeof(uint64_t);
+    return sizeof(ElimSmem<W>) + (size_t)n * basis_stride<W>() * sizeof(uint64_t);
 }
 
 // Step (1) for the whole CTA: the reduced row echelon form, pivots and the
@@ -170,11 +170,11 @@ constexpr size_t elim_smem_bytes(int n)
 // and the input checks are left to the other CTAs and kernel. Also
 // zeroes the z^a rows of both tables (factor_kvec_kernel ORs the bits in) and
 // the scratch words the second kernel uses, and publishes r in work[kWorkR].
-template <int W, int R, int NW>
+template <int W, int R>
 __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const FactorOut& o, unsigned char* smem)
 {
     constexpr int kNone = 0x7fffffff;
-    using Smem = ElimSmem<W, NW>;
+    using Smem = ElimSmem<W>;
     Smem& sm = *reinterpret_cast<Smem*>(smem);
     constexpr int SW = basis_stride<W>();
     uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem + sizeof(Smem));  // [n][SW]
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(512, 1) factor_elim_kernel(const uint64_t* __r
         check_input<W>(A, n, (int)blockIdx.x - 1, (int)gridDim.x - 1, o.work);
         return;
     }
-    eliminate_only<W, rows_per_thread<W>(), 16>(A, n, o, smem);
+    eliminate_only<W, rows_per_thread<W>()>(A, n, o, smem);
 }
 
 // Steps (2)-(4), one CTA per free column f (the j-th free column, j =
@@ -571,13 +571,13 @@ hlf_status launch_factor_large(const uint64_t* A, int n, const FactorOut& o, cud
     constexpr int R = rows_per_thread<W>();
     if (!o.work) return HLF_ERR_INTERNAL;
     const int threads = ((n + R - 1) / R + 31) / 32 * 32;
-    const size_t smem = elim_smem_bytes<W, 16>(n);
+    const size_t smem = elim_smem_bytes<W>(n);
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_set[dev]) {
         if (cudaFuncSetAttribute(factor_elim_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)elim_smem_bytes<W, 16>(HLF_MAX_N)) != cudaSuccess)
+                                 (int)elim_smem_bytes<W>(HLF_MAX_N)) != cudaSuccess)
             return HLF_ERR_CUDA;
         attr_set[dev] = true;
     }

@@ -16,7 +16,7 @@
 //                        kernel vector x_f, q(x_f) mod 4 and the bit z^a_f
 //                        (steps (2)-(4)), the paper-order table, and, in
 //                        the last CTA to finish, the status and rank.
-// At n = 1024 (grid 32 x 32) this takes 304 us; one CTA running
+// At n = 1024 (grid 32 x 32) this takes 296 us; one CTA running
 // factor_block's column loop for everything took 392 us. Against the one-CTA
 // path it saves 4-12% from W = 7 on (n = 400: 99 us against 105; n = 512:
 // 123 us against 140), ties at W = 6 and loses at W = 5 (n = 289: 70 us
@@ -242,9 +242,10 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
             }
             if (tid < 32) sm.colidx[tid] = -1;  // read last before the previous panel's update barrier
             int kp = 0;
-            // rolled: 2W copies of the panel code suit the instruction
-            // cache, 64W copies of this body would not
-#pragma unroll 1
+            // unrolled by 4 only: 2W copies of the panel code suit the
+            // instruction cache, 64W copies of this body would not (by 4:
+            // the search 5% faster than rolled at n = 1024)
+#pragma unroll 4
             for (int b = 0; b < ncols; ++b) {
                 const int buf = b & 1;
                 int cand = kNone;

@@ -23,11 +23,12 @@
 // against 67), hence the threshold.
 //
 // Where the elimination's time goes at n = 1024 (random symmetric, full
-// rank; clock64 phase counters, 667k cycles): the pivot search 365k (356
-// cycles a column), the inversions 127k, the table updates 158k, the tables
+// rank; clock64 phase counters, 617k cycles): the pivot search 348k (340
+// cycles a column), the inversions 91k, the table updates ~155k, the tables
 // 26k. The search is one CTA barrier per column and is bound by the issue of
-// its 16 warps: each column costs every warp its candidate, two warp
-// minima, the exchange and the slice updates. Measured at n = 1024 and
+// its 16 warps and the chain through the exchange: each column costs every
+// warp its candidate, two warp minima, the exchange and the slice updates.
+// Measured at n = 1024 and
 // dropped:
 //   - factor_block's loop (every row's full row XORs the pivot row each
 //     column, 600 cycles a column): 355 us;

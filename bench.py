@@ -73,7 +73,7 @@ KERNEL_SOURCES = {
 TRAFFIC = {  # kernel -> per-launch DRAM bytes (read + write) and the source digest at capture
     "reduce_kernel<1,6,1024>": {"bytes": 541440 + 1536, "sources": "0b975b98a6be7595"},
     "store_kernel<1,2>": {"bytes": 244992 + 8525198848, "sources": "0b975b98a6be7595"},
-    "dense1_kernel<16,1,1>": {"bytes": 630528 + 4767081216, "sources": "5acb1cca73b98019"},
+    "dense1_kernel<16,1,1>": {"bytes": 467200 + 4767411200, "sources": "2a92c04830996b04"},
 }
 
 

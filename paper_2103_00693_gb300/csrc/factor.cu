@@ -1,10 +1,10 @@
 // Stage 1 for one matrix (the CLA module of Section 2, steps (1)-(4)).
 //
-// n <= 384 (W <= 6): one CTA runs factor_block (factor_impl.cuh): input
+// n <= 256 (W <= 4): one CTA runs factor_block (factor_impl.cuh): input
 // checks, elimination, kernel vectors, q and z^a in one launch, which is what
 // the latency of small and medium instances wants.
 //
-// n > 384 (W >= 7): the same results from two launches that spread the work
+// n > 256 (W >= 5): the same results from two launches that spread the work
 // that does not have to be sequential over many SMs:
 //   factor_elim_kernel   CTA 0 runs the Gauss-Jordan elimination (step (1))
 //                        with the rows of A in registers, in panels of 32
@@ -16,18 +16,20 @@
 //                        kernel vector x_f, q(x_f) mod 4 and the bit z^a_f
 //                        (steps (2)-(4)), the paper-order table, and, in
 //                        the last CTA to finish, the status and rank.
-// At n = 1024 (grid 32 x 32) this takes 296 us; one CTA running
-// factor_block's column loop for everything took 392 us. Against the one-CTA
-// path it saves 4-12% from W = 7 on (n = 400: 99 us against 105; n = 512:
-// 123 us against 140), ties at W = 6 and loses at W = 5 (n = 289: 70 us
-// against 67), hence the threshold.
+// At n = 1024 this takes 269 us (grid 32 x 32) and 301 us (random symmetric);
+// one CTA running factor_block's column loop for everything took 392 us.
+// Against the one-CTA path it saves 9-20% from W = 5 on (n = 289: 53 us
+// against 60; n = 324: 59 against 70; n = 384: 73 against 78), ties at n =
+// 256 and loses below (n = 200: 42 us against 39), hence the threshold.
 //
 // Where the elimination's time goes at n = 1024 (random symmetric, full
-// rank; clock64 phase counters, 617k cycles): the pivot search 348k (340
-// cycles a column), the inversions 91k, the table updates ~155k, the tables
-// 26k. The search is one CTA barrier per column and is bound by the issue of
-// its 16 warps and the chain through the exchange: each column costs every
-// warp its candidate, two warp minima, the exchange and the slice updates.
+// rank; clock64 phase counters, 575k cycles): the pivot search 394k (384
+// cycles a column), the pivot rows' copy and the T2 tables 33k, the row
+// updates 141k. The search is one CTA barrier per column and is bound by the
+// issue of its 16 warps and the chain through the exchange: each column
+// costs every warp its candidate, two warp minima, the exchange and the
+// slice and record updates. The records replaced a Gauss-Jordan inversion of
+// each panel's pivot slices by one warp (91k cycles in all; 617k before).
 // Measured at n = 1024 and
 // dropped:
 //   - factor_block's loop (every row's full row XORs the pivot row each
@@ -35,8 +37,10 @@
 //   - a split barrier (an mbarrier whose arrive precedes the XOR of the
 //     previous pivot row's later words, and whose wait follows it): 607 us;
 //   - panels of 8 columns searched on 8-bit slices: 367 us;
-//   - panels of 64 columns with 64-bit slices and a per-row record of the
-//     absorbed pivots instead of the inversion: 395 us;
+//   - panels of 64 columns with 64-bit slices and per-row records: 395 us;
+//   - the exchange by a shared atomicMin per warp into a per-column slot
+//     instead of per-warp slots and a second warp minimum: the search 462k
+//     cycles against 394k;
 //   - two columns per barrier (each warp offering its lowest rows with bit
 //     0, with bit 1 and with bit 0 xor bit 1 set, which settles the pivots
 //     of both columns): 345 us, the search 405 cycles a column;
@@ -82,7 +86,7 @@ hlf_status launch_factor_w(const uint64_t* A, int n, const FactorOut& o, cudaStr
     return cudaGetLastError() == cudaSuccess ? HLF_OK : HLF_ERR_CUDA;
 }
 
-// ------------------------------------------------------------ n > 384
+// ------------------------------------------------------------ n > 256
 
 constexpr int kChkCtas = 8;       // CTAs that check the input beside the elimination
 constexpr int kWorkR = 16;        // work[16] = r
@@ -93,68 +97,11 @@ constexpr int kKvecCtas = 256;    // CTAs of factor_kvec_kernel (one free column
 static_assert(kWorkMask + HLF_MAX_N / 32 <= kFactorWorkWords, "the pivot mask fits the scratch words");
 static_assert(kChkCtas <= kWorkR, "one status slot per checking CTA");
 
-// Transpose a 32 x 32 bit block held by one warp: lane l has row l, bit s of
-// a row being column s. Stage j (j = 16, ..., 1) exchanges the bits at column
-// s + j of row t with those at column s of row t + j, for s and t with bit j
-// clear (lanes l and l ^ j pair up); the five stages compose to the transpose.
-__device__ __forceinline__ uint32_t transpose32_warp(uint32_t x, int lane)
-{
-#pragma unroll
-    for (int j = 16; j >= 1; j >>= 1) {
-        const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
-                         : j == 2  ? 0x33333333u : 0x55555555u;
-        const bool upper = (lane & j) != 0;
-        const uint32_t o = __shfl_xor_sync(0xffffffffu, x, j);
-        const uint32_t t = upper ? (((o >> j) ^ x) & m) : (((x >> j) ^ o) & m);
-        x ^= upper ? t : t << j;
-    }
-    return x;
-}
-
-// Step (b) of a panel, by warp 0: Gauss-Jordan of the kp pivot rows' start
-// slices st_piv on the pivot columns (colidx[b] >= 0), held by columns: lane
-// c has column c of the slices (bit k = slice k's bit c) and column c of the
-// augmented identity. A step reads one column by a shuffle; the row it picks
-// and the rows it changes are then known to every lane, each updating its
-// own column. H[colidx[b]] receives the row of the inverse that yields the
-// reduced pivot row of column b, over the pivot indices. Kept out of line:
-// one copy serves all 2W panels (the instruction cache holds it).
-__device__ __noinline__ void invert_panel(int kp, const uint32_t* st_piv, const int* colidx, uint32_t* H, int lane)
-{
-    const int ci = colidx[lane];
-    const unsigned pmask = __ballot_sync(0xffffffffu, ci >= 0);
-    uint32_t col = transpose32_warp(lane < kp ? st_piv[lane] : 0u, lane);
-    uint32_t hcol = lane < kp ? (1u << lane) : 0u;
-    uint32_t done = 0u;   // rows already holding a pivot column
-    uint32_t mybit = 1u;  // lane b: the row that holds pivot column b, as a bit
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {  // branch-free: a free column picks no row
-        const uint32_t colb = __shfl_sync(0xffffffffu, col, b);
-        const uint32_t cand = colb & ~done & (0u - ((pmask >> b) & 1u));
-        const uint32_t lb = cand & (0u - cand);  // the lowest such row
-        done |= lb;
-        if (lane == b && lb) mybit = lb;
-        const uint32_t rows = colb & ~lb;  // the rows that absorb it
-        if (col & lb) col ^= rows;
-        if (hcol & lb) hcol ^= rows;
-    }
-    // row L of the augmented part, over the pivot indices, is H of the pivot
-    // column L holds
-    const uint32_t hrow = transpose32_warp(hcol, lane);
-    const uint32_t hv = __shfl_sync(0xffffffffu, hrow, __ffs(mybit) - 1);
-    if (ci >= 0) H[ci] = hv;
-}
-
 template <int W>
 struct ElimSmem {
     int first[2][32];          // per warp: its lowest candidate's key, by column parity
-    uint32_t cw[2][32];        // and that row's current slice
-    uint32_t st_piv[32];       // the panel's pivot rows' slices at the panel's start
-    uint32_t H[32];            // their inverse on the pivot columns, over pivot indices
-    int colidx[32];            // pivot index of each column of the panel, -1 if free
+    uint2 cw[2][32];           // and that row's current slice and record, pivot bit added
     uint32_t pivmask[HLF_MAX_N / 32];  // the pivot columns, for the second kernel
-    signed char rowpiv[HLF_MAX_N];  // pivot index of each row in the panel, -1 otherwise
-    uint32_t T1[8 * 16];       // coefficient tables over the start slice's nibbles
     uint64_t piv[32][W];       // the pivot rows at the panel's start
     uint64_t T2[8 * 16 * (W | 1)];  // their combinations over 4 pivot indices, odd stride
     int pivcol[HLF_MAX_N];
@@ -193,34 +140,33 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
         for (int w = 0; w < W; ++w) row[j][w] = i < n ? A[(size_t)i * W + w] : 0ull;
     }
     // key = (row << 5) | warp; the rows past n are never candidates
-    constexpr int kNever = kNone - 1;
+    // key = (row << 5) | warp while the row may still become a pivot; kNone
+    // for the rows past n and for the pivot rows of earlier panels
     int key[R];
     bool used[R];
     int my_k[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        key[j] = tid + j * bs < n ? (((tid + j * bs) << 5) | warp) : kNever;
+        key[j] = tid + j * bs < n ? (((tid + j * bs) << 5) | warp) : kNone;
         used[j] = false;
         my_k[j] = -1;
     }
     if (tid < 64) (&sm.first[0][0])[tid] = kNone;  // the slots of absent warps stay empty
-    for (int i = tid; i < HLF_MAX_N; i += bs) sm.rowpiv[i] = -1;
     __syncthreads();
 
-    // Panels of 32 columns. (a) Pivot search on the rows' 32-bit slices: for
-    // each column the lowest unused row with the bit becomes the pivot and
-    // every slice with the bit absorbs the pivot's (the pivot's own slice
-    // turns to zero, so it is never a candidate again); the slices rotate
-    // so that bit 0 is the column. (b) One warp inverts the pivots' start
-    // slices restricted to the pivot columns: row k of the inverse (H_k)
-    // says which pivot start rows XOR to the fully reduced pivot row k.
-    // (c) Every row is rebuilt from the panel's start values: a pivot row
-    // as the XOR of the start rows in H_k, any other row as itself XOR the
-    // reduced pivot rows of the pivot columns its start slice has, whose
-    // start-row combination is read from nibble tables of H (T1). The
-    // result has zeros on the panel's pivot columns and spans the same rows,
-    // so it is the Gauss-Jordan elimination of the panel; the pivot rows are
-    // zero left of the panel, so only words w.. change.
+    // Panels of 32 columns. (a) Gauss-Jordan on the rows' 32-bit slices:
+    // for each column the lowest row with the bit that is not yet a pivot
+    // becomes the pivot, and every other slice with the bit, earlier pivots
+    // included, absorbs the pivot's; the slices rotate so that bit 0 is the
+    // column. Each row also keeps the record cf of what it absorbed, as a
+    // set of the panel's pivot rows taken at the panel's start: the pivot of
+    // index k publishes its own record with bit k added, and an absorbing row
+    // XORs that into its record. (b) Every row is rebuilt from the panel's
+    // start values as itself XOR the start rows of the pivots in its record,
+    // read from nibble tables of those start rows (T2). The result is the
+    // Gauss-Jordan elimination of the panel: zeros on its pivot columns
+    // outside each pivot's own row, the same span; the pivot rows are zero
+    // left of the panel, so only words w.. change.
     constexpr int kHalvesUnroll = W > 11 ? 2 : 1;
     int rank = 0;
 #pragma unroll
@@ -233,15 +179,14 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
             const int c0 = (w << 6) + (h << 5);
             if (c0 >= n) break;
             const int ncols = n - c0 < 32 ? n - c0 : 32;
-            uint32_t st[R], s[R];
+            uint32_t s[R], cf[R];
             int my_kp[R];
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                st[j] = (uint32_t)(row[j][w] >> (32 * h));
-                s[j] = used[j] ? 0u : st[j];
+                s[j] = (uint32_t)(row[j][w] >> (32 * h));
+                cf[j] = 0u;
                 my_kp[j] = -1;
             }
-            if (tid < 32) sm.colidx[tid] = -1;  // read last before the previous panel's update barrier
             int kp = 0;
             // unrolled by 4 only: 2W copies of the panel code suit the
             // instruction cache, 64W copies of this body would not (by 4:
@@ -254,90 +199,66 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
                 for (int j = 0; j < R; ++j) cand = min(cand, (s[j] & 1u) ? key[j] : kNone);
                 const int wmin = __reduce_min_sync(0xffffffffu, cand);
                 if (cand == wmin && wmin != kNone) {  // the lane of the warp's candidate
-                    uint32_t sv = s[0];
+                    uint32_t sv = s[0], cv = cf[0];
 #pragma unroll
-                    for (int j = 1; j < R; ++j) sv = cand == key[j] ? s[j] : sv;
-                    sm.cw[buf][warp] = sv;
+                    for (int j = 1; j < R; ++j) {
+                        sv = cand == key[j] ? s[j] : sv;
+                        cv = cand == key[j] ? cf[j] : cv;
+                    }
+                    sm.cw[buf][warp] = make_uint2(sv, cv ^ (1u << kp));
                 }
                 if (lane == 0) sm.first[buf][warp] = wmin;
                 __syncthreads();
                 const int pk = __reduce_min_sync(0xffffffffu, sm.first[buf][lane]);
-                // no row has bit 0 set when the column has no pivot
-                const uint32_t ps = pk != kNone ? sm.cw[buf][pk & 31] : 0u;
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const uint32_t t = (s[j] & 1u) ? s[j] ^ ps : s[j];
-                    s[j] = __funnelshift_r(t, t, 1);
-                }
                 if (pk != kNone) {  // uniform
-                    if (tid == 0) {
-                        sm.colidx[b] = kp;
-                        if (HLF_IN_BOUNDS(rank + kp, HLF_MAX_N, kSiteFactorSmem)) sm.pivcol[rank + kp] = c0 + b;
-                        if (HLF_IN_BOUNDS(pk >> 5, HLF_MAX_N, kSiteFactorSmem)) sm.rowpiv[pk >> 5] = (signed char)kp;
+                    const uint2 pv = sm.cw[buf][pk & 31];
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        const bool me = key[j] == pk;
+                        const bool ab = (s[j] & 1u) && !me;
+                        s[j] = ab ? s[j] ^ pv.x : s[j];
+                        cf[j] = ab ? cf[j] ^ pv.y : cf[j];
+                        my_kp[j] = me ? kp : my_kp[j];
+                        key[j] = me ? kNone : key[j];
                     }
+                    if (tid == 0 && HLF_IN_BOUNDS(rank + kp, HLF_MAX_N, kSiteFactorSmem))
+                        sm.pivcol[rank + kp] = c0 + b;
                     ++kp;
                 }
+#pragma unroll
+                for (int j = 0; j < R; ++j) s[j] = __funnelshift_r(s[j], s[j], 1);
             }
-            __syncthreads();  // rowpiv complete
-            // the pivot rows: start slice and start row (words w..) to the tables
+            if (kp == 0) continue;  // uniform; nothing absorbed anything
+            // the pivot rows' start rows (words w..) to the table's source
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                if (key[j] == kNever) continue;
-                const int k = sm.rowpiv[tid + j * bs];
+                const int k = my_kp[j];
                 if (k < 0 || !HLF_IN_BOUNDS(k, 32, kSiteFactorSmem)) continue;
-                sm.rowpiv[tid + j * bs] = -1;
-                my_kp[j] = k;
                 used[j] = true;
                 my_k[j] = rank + k;
-                sm.st_piv[k] = st[j];
 #pragma unroll
                 for (int v = w; v < W; ++v) sm.piv[k][v] = row[j][v];
             }
             rank += kp;
             __syncthreads();
-            if (kp == 0) continue;  // uniform
             const int V = W - w;
             const int VP = V | 1;  // odd stride: the 16 entries of a table in distinct banks
-            if (warp == 0) {
-                invert_panel(kp, sm.st_piv, sm.colidx, sm.H, lane);
-            } else {
-                // T2[(t, x)][v]: XOR of the start rows' word w + v of the pivots
-                // 4t + i, i over the bits of x
-                for (int e = tid - 32; e < 128 * V; e += bs - 32) {
-                    const int v = e % V;
-                    const int tx = e / V;
-                    const int k0 = (tx >> 4) << 2;
-                    uint64_t acc = 0ull;
+            // T2[(t, x)][v]: XOR of the start rows' word w + v of the pivots
+            // 4t + i, i over the bits of x
+            for (int e = tid; e < 128 * V; e += bs) {
+                const int v = e % V;
+                const int tx = e / V;
+                const int k0 = (tx >> 4) << 2;
+                uint64_t acc = 0ull;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (((tx >> i) & 1) && k0 + i < kp) acc ^= sm.piv[k0 + i][w + v];
-                    if (HLF_IN_BOUNDS(tx * VP + v, 128 * (W | 1), kSiteFactorSmem)) sm.T2[tx * VP + v] = acc;
-                }
-            }
-            __syncthreads();
-            if (tid < 128) {  // T1[(t, x)]: XOR of H over the pivot columns 4t + i, i over the bits of x
-                const int t = tid >> 4;
-                uint32_t acc = 0u;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int j = sm.colidx[4 * t + i];
-                    if (((tid >> i) & 1) && j >= 0) acc ^= sm.H[j];
-                }
-                sm.T1[tid] = acc;
+                for (int i = 0; i < 4; ++i)
+                    if (((tx >> i) & 1) && k0 + i < kp) acc ^= sm.piv[k0 + i][w + v];
+                if (HLF_IN_BOUNDS(tx * VP + v, 128 * (W | 1), kSiteFactorSmem)) sm.T2[tx * VP + v] = acc;
             }
             __syncthreads();
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                uint32_t coef;
-                if (my_kp[j] >= 0) {
-                    coef = sm.H[my_kp[j]];
-#pragma unroll
-                    for (int v = w; v < W; ++v) row[j][v] = 0ull;
-                } else {
-                    coef = 0u;
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) coef ^= sm.T1[(t << 4) | ((st[j] >> (4 * t)) & 15u)];
-                }
+                const uint32_t coef = cf[j];
                 const uint64_t* tb[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) tb[t] = sm.T2 + ((t << 4) | (int)((coef >> (4 * t)) & 15u)) * VP;
@@ -347,7 +268,7 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
                                      ((tb[4][v] ^ tb[5][v]) ^ (tb[6][v] ^ tb[7][v]));
             }
             // the next panel's first column barrier orders these reads before
-            // H, T1 and T2 are written again
+            // piv and T2 are written again
         }
     }
     const int r = rank;
@@ -598,8 +519,8 @@ hlf_status launch_factor(const uint64_t* A, int n, int W, const FactorOut& o, cu
     case 2: return launch_factor_w<2>(A, n, o, s);
     case 3: return launch_factor_w<3>(A, n, o, s);
     case 4: return launch_factor_w<4>(A, n, o, s);
-    case 5: return launch_factor_w<5>(A, n, o, s);
-    case 6: return launch_factor_w<6>(A, n, o, s);
+    case 5: return launch_factor_large<5>(A, n, o, s);
+    case 6: return launch_factor_large<6>(A, n, o, s);
     case 7: return launch_factor_large<7>(A, n, o, s);
     case 8: return launch_factor_large<8>(A, n, o, s);
     case 9: return launch_factor_large<9>(A, n, o, s);

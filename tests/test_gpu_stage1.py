@@ -25,7 +25,7 @@ def _cases():
     for n in (1, 64, 100, 1024):
         c.append((f"zero{n}", np.zeros((n, n), dtype=np.uint8)))
         c.append((f"eye{n}", np.eye(n, dtype=np.uint8)))
-    for n in (192, 193, 250, 256, 257, 320):  # last one-warp widths (W <= 4), first CTA widths
+    for n in (192, 193, 250, 256, 257, 320):  # the one-CTA path's last widths (W <= 4), the panel path's first
         c.append((f"sym{n}", synth.random_symmetric(n, 0.5, n)))
     # pivots only among late rows: the first rows and columns are zero
     for n, z in ((40, 33), (100, 50), (256, 200), (700, 600)):
@@ -40,12 +40,21 @@ def _cases():
         c.append((f"lowrank{n}-{k}", ((X @ X.T) & 1).astype(np.uint8)))
     c.append(("sparse300", synth.random_symmetric(300, 0.01, 3)))
     c.append(("dense1000", synth.random_symmetric(1000, 0.9, 4)))
-    # the panel path's lower end (W = 7, 8: n = 385..512) and its boundary
-    for N in (20, 22):
+    # the panel path from its lower end (W = 5: n = 257..320) to W = 8, and
+    # the word boundaries on the way
+    for N in (17, 18, 20, 22):
         c.append((f"grid{N}-p.5", synth.grid_instance(N, 0.5, 30 + N)))
         c.append((f"grid{N}-full", synth.grid_instance(N, 1.0, 40 + N)))
-    for n in (384, 385, 448, 449):
+    for n in (258, 288, 321, 384, 385, 448, 449):
         c.append((f"sym{n}", synth.random_symmetric(n, 0.5, n)))
+    A = synth.random_symmetric(300, 0.5, 71)
+    A[:270, :] = 0
+    A[:, :270] = 0
+    c.append(("late300-270", A))
+    X = np.random.default_rng(9).integers(0, 2, size=(280, 10), dtype=np.int64)
+    c.append(("lowrank280-10", ((X @ X.T) & 1).astype(np.uint8)))
+    c.append(("zero260", np.zeros((260, 260), dtype=np.uint8)))
+    c.append(("eye330", np.eye(330, dtype=np.uint8)))
     A = synth.random_symmetric(500, 0.5, 77)
     A[:400, :] = 0
     A[:, :400] = 0
@@ -87,7 +96,8 @@ def test_factor_rejects_non_symmetric(cuda_ok):
 
 ASYM = [(64, 0, 63), (64, 40, 7), (100, 99, 64), (100, 64, 99), (100, 70, 10),
         (1000, 0, 999), (1000, 999, 0), (1000, 500, 501), (1000, 37, 485), (1000, 63, 64),
-        (1000, 960, 999), (1000, 33, 2), (1024, 1023, 1022), (1024, 96, 1000)]
+        (1000, 960, 999), (1000, 33, 2), (1024, 1023, 1022), (1024, 96, 1000),
+        (300, 299, 257), (300, 10, 290)]
 
 
 @pytest.mark.parametrize("n,i,j", ASYM, ids=[f"n{n}-{i}-{j}" for n, i, j in ASYM])

@@ -16,20 +16,24 @@
 //                        kernel vector x_f, q(x_f) mod 4 and the bit z^a_f
 //                        (steps (2)-(4)), the paper-order table, and, in
 //                        the last CTA to finish, the status and rank.
-// At n = 1024 this takes 269 us (grid 32 x 32) and 301 us (random symmetric);
-// one CTA running factor_block's column loop for everything took 392 us.
-// Against the one-CTA path it saves 9-20% from W = 5 on (n = 289: 53 us
-// against 60; n = 324: 59 against 70; n = 384: 73 against 78), ties at n =
-// 256 and loses below (n = 200: 42 us against 39), hence the threshold.
+// At n = 1024 this takes 202 us (grid 32 x 32) and 309 us (random
+// symmetric); one CTA running factor_block's column loop for everything took
+// 392 us. Against the one-CTA path it saves 11-19% on grids from W = 5 on
+// (n = 289: 53 us against 60; n = 324: 57 against 70; n = 361: 63 against
+// 74), ties on random symmetric matrices there (n = 300: 57.4 against 57.7;
+// n = 384: 76.7 against 78.4), ties at n = 256 and loses below (n = 200: 42
+// us against 39), hence the threshold.
 //
-// Where the elimination's time goes at n = 1024 (random symmetric, full
-// rank; clock64 phase counters, 575k cycles): the pivot search 394k (384
-// cycles a column), the pivot rows' copy and the T2 tables 33k, the row
-// updates 141k. The search is one CTA barrier per column and is bound by the
-// issue of its 16 warps and the chain through the exchange: each column
-// costs every warp its candidate, two warp minima, the exchange and the
-// slice and record updates. The records replaced a Gauss-Jordan inversion of
-// each panel's pivot slices by one warp (91k cycles in all; 617k before).
+// The elimination's cost is the pivot search: a CTA barrier per column and
+// the chain through the exchange (every searching warp's candidate, two warp
+// minima, the exchange, the slice and record updates). Per-row records of the
+// absorbed pivots replaced a Gauss-Jordan inversion of each panel's pivot
+// slices by one warp (91k of 617k cycles at n = 1024). Keeping the pivot rows
+// of earlier panels out of the search, and with them every warp that holds no
+// live slice, leaves two or three searching warps a panel on grids (grid 32 x
+// 32: 269 -> 202 us) at the price of a barrier and the T1 tables a panel on
+// dense matrices (random symmetric n = 1024: 301 -> 309 us).
+//
 // Measured at n = 1024 and
 // dropped:
 //   - factor_block's loop (every row's full row XORs the pivot row each
@@ -41,6 +45,11 @@
 //   - the exchange by a shared atomicMin per warp into a per-column slot
 //     instead of per-warp slots and a second warp minimum: the search 462k
 //     cycles against 394k;
+//   - one copy of the panel code for all panels (the word w picked out of
+//     the registers by unrolled selects, the updates predicated on v >= w):
+//     grid 32 x 32 214 us against 202, random symmetric 327 against 309;
+//   - the table builds in one out-of-line function: 218 us against 202 (the
+//     call saves and restores the live registers);
 //   - two columns per barrier (each warp offering its lowest rows with bit
 //     0, with bit 1 and with bit 0 xor bit 1 set, which settles the pivots
 //     of both columns): 345 us, the search 405 cycles a column;
@@ -101,6 +110,11 @@ template <int W>
 struct ElimSmem {
     int first[2][32];          // per warp: its lowest candidate's key, by column parity
     uint2 cw[2][32];           // and that row's current slice and record, pivot bit added
+    int part[32];              // per warp: whether it holds a live slice in the panel
+    int npiv;                  // the panel's pivot count, from the searching warps
+    int colidx[32];            // pivot index of each column of the panel, -1 if free
+    uint32_t H[32];            // reduced pivot row k as a set of the panel's pivot start rows
+    uint32_t T1[8 * 16];       // XORs of H over 4 pivot columns, for the earlier pivot rows
     uint32_t pivmask[HLF_MAX_N / 32];  // the pivot columns, for the second kernel
     uint64_t piv[32][W];       // the pivot rows at the panel's start
     uint64_t T2[8 * 16 * (W | 1)];  // their combinations over 4 pivot indices, odd stride
@@ -151,22 +165,29 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
         used[j] = false;
         my_k[j] = -1;
     }
-    if (tid < 64) (&sm.first[0][0])[tid] = kNone;  // the slots of absent warps stay empty
+    if (tid < 64) (&sm.first[0][0])[tid] = kNone;
+    if (tid < 32) sm.part[tid] = 0;  // absent warps never search
     __syncthreads();
 
-    // Panels of 32 columns. (a) Gauss-Jordan on the rows' 32-bit slices:
-    // for each column the lowest row with the bit that is not yet a pivot
-    // becomes the pivot, and every other slice with the bit, earlier pivots
-    // included, absorbs the pivot's; the slices rotate so that bit 0 is the
-    // column. Each row also keeps the record cf of what it absorbed, as a
-    // set of the panel's pivot rows taken at the panel's start: the pivot of
-    // index k publishes its own record with bit k added, and an absorbing row
-    // XORs that into its record. (b) Every row is rebuilt from the panel's
-    // start values as itself XOR the start rows of the pivots in its record,
-    // read from nibble tables of those start rows (T2). The result is the
-    // Gauss-Jordan elimination of the panel: zeros on its pivot columns
-    // outside each pivot's own row, the same span; the pivot rows are zero
-    // left of the panel, so only words w.. change.
+    // Panels of 32 columns. (a) Gauss-Jordan on the 32-bit slices of the
+    // rows that are not pivots of earlier panels: for each column the lowest
+    // such row with the bit that is not yet a pivot becomes the pivot, and
+    // every other slice with the bit, the panel's earlier pivots included,
+    // absorbs the pivot's; the slices rotate so that bit 0 is the column.
+    // Each row also keeps the record cf of what it absorbed, as a set of the
+    // panel's pivot rows taken at the panel's start: the pivot of index k
+    // publishes its own record with bit k added, and an absorbing row XORs
+    // that into its record. Only the warps holding a nonzero slice search,
+    // behind a named barrier sized to them (on banded matrices, two or three
+    // warps). (b) The reduced pivot row k is the set H_k = its final record
+    // plus k. Every row is rebuilt from the panel's start values as itself
+    // XOR the start rows of the pivots in its record, read from nibble tables
+    // of those start rows (T2); a pivot row of an earlier panel takes, as its
+    // record, the XOR of H over the pivot columns its start slice has (nibble
+    // tables T1 of H). The result is the Gauss-Jordan elimination of the
+    // panel: zeros on its pivot columns outside each pivot's own row, the same
+    // span; the pivot rows are zero left of the panel, so only words w..
+    // change.
     constexpr int kHalvesUnroll = W > 11 ? 2 : 1;
     int rank = 0;
 #pragma unroll
@@ -181,66 +202,85 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
             const int ncols = n - c0 < 32 ? n - c0 : 32;
             uint32_t s[R], cf[R];
             int my_kp[R];
+            bool live = false;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                s[j] = (uint32_t)(row[j][w] >> (32 * h));
+                s[j] = used[j] ? 0u : (uint32_t)(row[j][w] >> (32 * h));
                 cf[j] = 0u;
                 my_kp[j] = -1;
+                live |= s[j] != 0u;
             }
+            live = __any_sync(0xffffffffu, live);
+            if (lane == 0) {
+                sm.part[warp] = live;
+                if (!live) sm.first[0][warp] = sm.first[1][warp] = kNone;  // read by the searching warps
+            }
+            if (tid < 32) sm.colidx[tid] = -1;
+            __syncthreads();  // also: the previous panel's table reads are done
+            const unsigned pm = __ballot_sync(0xffffffffu, sm.part[lane] != 0);
             int kp = 0;
-            // unrolled by 4 only: 2W copies of the panel code suit the
-            // instruction cache, 64W copies of this body would not (by 4:
-            // the search 5% faster than rolled at n = 1024)
+            if ((pm >> warp) & 1u) {  // warp-uniform
+                const int nthr = __popc(pm) * 32;
+                const bool scribe = lane == 0 && warp == __ffs(pm) - 1;  // the lowest searching warp's lane 0
+                // unrolled by 4 only: 2W copies of the panel code suit the
+                // instruction cache, 64W copies of this body would not (by 4:
+                // the search 5% faster than rolled at n = 1024)
 #pragma unroll 4
-            for (int b = 0; b < ncols; ++b) {
-                const int buf = b & 1;
-                int cand = kNone;
+                for (int b = 0; b < ncols; ++b) {
+                    const int buf = b & 1;
+                    int cand = kNone;
 #pragma unroll
-                for (int j = 0; j < R; ++j) cand = min(cand, (s[j] & 1u) ? key[j] : kNone);
-                const int wmin = __reduce_min_sync(0xffffffffu, cand);
-                if (cand == wmin && wmin != kNone) {  // the lane of the warp's candidate
-                    uint32_t sv = s[0], cv = cf[0];
+                    for (int j = 0; j < R; ++j) cand = min(cand, (s[j] & 1u) ? key[j] : kNone);
+                    const int wmin = __reduce_min_sync(0xffffffffu, cand);
+                    if (cand == wmin && wmin != kNone) {  // the lane of the warp's candidate
+                        uint32_t sv = s[0], cv = cf[0];
 #pragma unroll
-                    for (int j = 1; j < R; ++j) {
-                        sv = cand == key[j] ? s[j] : sv;
-                        cv = cand == key[j] ? cf[j] : cv;
+                        for (int j = 1; j < R; ++j) {
+                            sv = cand == key[j] ? s[j] : sv;
+                            cv = cand == key[j] ? cf[j] : cv;
+                        }
+                        sm.cw[buf][warp] = make_uint2(sv, cv ^ (1u << kp));
                     }
-                    sm.cw[buf][warp] = make_uint2(sv, cv ^ (1u << kp));
-                }
-                if (lane == 0) sm.first[buf][warp] = wmin;
-                __syncthreads();
-                const int pk = __reduce_min_sync(0xffffffffu, sm.first[buf][lane]);
-                if (pk != kNone) {  // uniform
-                    const uint2 pv = sm.cw[buf][pk & 31];
+                    if (lane == 0) sm.first[buf][warp] = wmin;
+                    asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+                    const int pk = __reduce_min_sync(0xffffffffu, sm.first[buf][lane]);
+                    if (pk != kNone) {  // uniform
+                        const uint2 pv = sm.cw[buf][pk & 31];
 #pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        const bool me = key[j] == pk;
-                        const bool ab = (s[j] & 1u) && !me;
-                        s[j] = ab ? s[j] ^ pv.x : s[j];
-                        cf[j] = ab ? cf[j] ^ pv.y : cf[j];
-                        my_kp[j] = me ? kp : my_kp[j];
-                        key[j] = me ? kNone : key[j];
+                        for (int j = 0; j < R; ++j) {
+                            const bool me = key[j] == pk;
+                            const bool ab = (s[j] & 1u) && !me;
+                            s[j] = ab ? s[j] ^ pv.x : s[j];
+                            cf[j] = ab ? cf[j] ^ pv.y : cf[j];
+                            my_kp[j] = me ? kp : my_kp[j];
+                            key[j] = me ? kNone : key[j];
+                        }
+                        if (scribe) {
+                            sm.colidx[b] = kp;
+                            if (HLF_IN_BOUNDS(rank + kp, HLF_MAX_N, kSiteFactorSmem)) sm.pivcol[rank + kp] = c0 + b;
+                        }
+                        ++kp;
                     }
-                    if (tid == 0 && HLF_IN_BOUNDS(rank + kp, HLF_MAX_N, kSiteFactorSmem))
-                        sm.pivcol[rank + kp] = c0 + b;
-                    ++kp;
-                }
 #pragma unroll
-                for (int j = 0; j < R; ++j) s[j] = __funnelshift_r(s[j], s[j], 1);
+                    for (int j = 0; j < R; ++j) s[j] = __funnelshift_r(s[j], s[j], 1);
+                }
+                if (scribe) sm.npiv = kp;
             }
-            if (kp == 0) continue;  // uniform; nothing absorbed anything
-            // the pivot rows' start rows (words w..) to the table's source
+            // the pivot rows: start rows (words w..) to T2's source, H_k
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 const int k = my_kp[j];
                 if (k < 0 || !HLF_IN_BOUNDS(k, 32, kSiteFactorSmem)) continue;
                 used[j] = true;
                 my_k[j] = rank + k;
+                sm.H[k] = cf[j] ^ (1u << k);
 #pragma unroll
                 for (int v = w; v < W; ++v) sm.piv[k][v] = row[j][v];
             }
-            rank += kp;
             __syncthreads();
+            kp = pm ? sm.npiv : 0;
+            if (kp == 0) continue;  // uniform; nothing absorbs anything
+            rank += kp;
             const int V = W - w;
             const int VP = V | 1;  // odd stride: the 16 entries of a table in distinct banks
             // T2[(t, x)][v]: XOR of the start rows' word w + v of the pivots
@@ -255,10 +295,26 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
                     if (((tx >> i) & 1) && k0 + i < kp) acc ^= sm.piv[k0 + i][w + v];
                 if (HLF_IN_BOUNDS(tx * VP + v, 128 * (W | 1), kSiteFactorSmem)) sm.T2[tx * VP + v] = acc;
             }
+            if (tid < 128) {  // T1[(t, x)]: XOR of H over the pivot columns 4t + i, i over the bits of x
+                const int t = tid >> 4;
+                uint32_t acc = 0u;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = sm.colidx[4 * t + i];
+                    if (((tid >> i) & 1) && k >= 0 && HLF_IN_BOUNDS(k, 32, kSiteFactorSmem)) acc ^= sm.H[k];
+                }
+                sm.T1[tid] = acc;
+            }
             __syncthreads();
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                const uint32_t coef = cf[j];
+                uint32_t coef = cf[j];
+                if (used[j] && my_kp[j] < 0) {  // a pivot row of an earlier panel
+                    const uint32_t st = (uint32_t)(row[j][w] >> (32 * h));
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) coef ^= sm.T1[(t << 4) | ((st >> (4 * t)) & 15u)];
+                }
+                if (!__any_sync(0xffffffffu, coef != 0u)) continue;  // warp-uniform
                 const uint64_t* tb[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) tb[t] = sm.T2 + ((t << 4) | (int)((coef >> (4 * t)) & 15u)) * VP;
@@ -267,8 +323,8 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
                     row[j][w + v] ^= ((tb[0][v] ^ tb[1][v]) ^ (tb[2][v] ^ tb[3][v])) ^
                                      ((tb[4][v] ^ tb[5][v]) ^ (tb[6][v] ^ tb[7][v]));
             }
-            // the next panel's first column barrier orders these reads before
-            // piv and T2 are written again
+            // the next panel's first barrier orders these reads before the
+            // tables are written again
         }
     }
     const int r = rank;

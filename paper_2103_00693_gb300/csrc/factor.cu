@@ -47,7 +47,9 @@
 //     cycles against 394k;
 //   - one copy of the panel code for all panels (the word w picked out of
 //     the registers by unrolled selects, the updates predicated on v >= w):
-//     grid 32 x 32 214 us against 202, random symmetric 327 against 309;
+//     grid 32 x 32 214 us against 202, random symmetric 327 against 309; with
+//     the table build free of divisions and the update dispatched to a copy
+//     per w instead of predicated, 211 and 326;
 //   - the table builds in one out-of-line function: 218 us against 202 (the
 //     call saves and restores the live registers);
 //   - two columns per barrier (each warp offering its lowest rows with bit

@@ -155,7 +155,6 @@ __device__ void eliminate_only(const uint64_t* __restrict__ A, int n, const Fact
 #pragma unroll
         for (int w = 0; w < W; ++w) row[j][w] = i < n ? A[(size_t)i * W + w] : 0ull;
     }
-    // key = (row << 5) | warp; the rows past n are never candidates
     // key = (row << 5) | warp while the row may still become a pivot; kNone
     // for the rows past n and for the pivot rows of earlier panels
     int key[R];
